@@ -1,0 +1,293 @@
+"""Pins of the CPU oracle to facts outside itself (no GPU).
+
+Each check targets a part of the oracle a plausible mistake could break:
+closed forms on complete, disjoint-union and complete multipartite graphs
+(binomials, sums, elementary symmetric polynomials), brute-force clique
+enumeration on random graphs (all three tables), matrix identities for
+triangles, the counting identities of Alg. 2 (sum of local counts), the
+unique-encoding theorem (Thm. scr) on explicit SCT paths, relabelling,
+truncation, the degeneracy order, textbook graphs, and multi-limb overflow.
+"""
+from __future__ import annotations
+
+import itertools
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2001_06784_gb300 import graphgen
+from tests import graphs
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "named_graphs.json")
+
+
+# ------------------------------------------------------------ brute force
+
+def all_cliques(row_ptr, col):
+    """Every non-empty clique, each once, grown in increasing vertex order
+    (plain backtracking, no pivoting, no orientation)."""
+    adj = graphs.adjacency_sets(row_ptr, col)
+    n = len(adj)
+    out = []
+
+    def grow(clique, cand):
+        for i, v in enumerate(cand):
+            c = clique + [v]
+            out.append(tuple(c))
+            grow(c, [u for u in cand[i + 1:] if u in adj[v]])
+
+    grow([], list(range(n)))
+    return out
+
+
+def brute_counts(row_ptr, col, K):
+    n = len(row_ptr) - 1
+    eid = {tuple(e): i for i, e in enumerate(graphgen.edge_list(row_ptr, col).tolist())}
+    C = [0] * (K + 1)
+    cv = [[0] * (K + 1) for _ in range(n)]
+    ce = [[0] * (K + 1) for _ in range(len(eid))]
+    for c in all_cliques(row_ptr, col):
+        k = len(c)
+        if k > K:
+            continue
+        C[k] += 1
+        for v in c:
+            cv[v][k] += 1
+        for a, b in itertools.combinations(c, 2):
+            ce[eid[(min(a, b), max(a, b))]][k] += 1
+    return C, cv, ce
+
+
+def esym(parts, k):
+    """Elementary symmetric polynomial e_k(parts)."""
+    return sum(math.prod(c) for c in itertools.combinations(parts, k))
+
+
+# ------------------------------------------------------------ closed forms
+
+@pytest.mark.parametrize("n", [1, 2, 3, 4, 7, 12, 33, 64])
+def test_complete_graph_all_tables(n):
+    rp, col = graphs.complete(n)
+    r = oracle.count(rp, col, vertex=True, edge=n <= 33)
+    K = r["kmax"]
+    assert r["C"] == [0] + [math.comb(n, k) for k in range(1, K + 1)]
+    cv = oracle.to_int(r["cv"])
+    for v in range(n):
+        assert cv[v] == [0] + [math.comb(n - 1, k - 1) for k in range(1, K + 1)]
+    if n <= 33:
+        for row in oracle.to_int(r["ce"]):
+            assert row == [0, 0] + [math.comb(n - 2, k - 2) for k in range(2, K + 1)]
+
+
+def test_complete_graph_many_limbs():
+    # C(250, 125) ~ 2^246: exercises carries across eight 32-bit limbs
+    n = 250
+    rp, col = graphs.complete(n)
+    r = oracle.count(rp, col)
+    assert r["nl"] >= 8
+    assert r["C"] == [0] + [math.comb(n, k) for k in range(1, n + 1)]
+
+
+@pytest.mark.parametrize("sizes", [[3, 5, 7, 4, 1, 2], [10, 10, 1, 1, 6], [30, 2, 17]])
+def test_disjoint_cliques(sizes):
+    rp, col = graphs.disjoint_cliques(sizes)
+    r = oracle.count(rp, col, vertex=True)
+    K = r["kmax"]
+    assert r["C"] == [0] + [sum(math.comb(a, k) for a in sizes) for k in range(1, K + 1)]
+    cv = oracle.to_int(r["cv"])
+    v = 0
+    for a in sizes:
+        for _ in range(a):
+            assert cv[v] == [0] + [math.comb(a - 1, k - 1) for k in range(1, K + 1)]
+            v += 1
+
+
+@pytest.mark.parametrize("parts", [[3, 3, 3, 3, 3, 3], [5, 4, 3, 2, 1], [1, 1, 1, 1], [7, 1], [2, 2, 2, 2, 2, 2, 2]])
+def test_complete_multipartite(parts):
+    rp, col = graphs.multipartite(parts)
+    r = oracle.count(rp, col)
+    K = r["kmax"]
+    assert r["C"] == [0] + [esym(parts, k) for k in range(1, K + 1)]
+
+
+def test_named_graphs_golden():
+    data = json.load(open(GOLDEN))
+    for g in data["graphs"]:
+        rp, col = graphgen.from_edges(g["n"], g["edges"])
+        r = oracle.count(rp, col)
+        C = r["C"] + [0] * 8
+        want = g["C"] + [0] * (len(r["C"]) + 8 - len(g["C"]))
+        assert C[:len(want)] == want[:len(C)], g["name"]
+
+
+# ------------------------------------------------------------ brute force
+
+@pytest.mark.parametrize("n,p,seed", [(12, 0.5, 0), (20, 0.5, 1), (30, 0.3, 2), (40, 0.2, 3), (18, 0.75, 4),
+                                      (25, 0.6, 5), (36, 0.4, 6)])
+def test_bruteforce_random_graphs(n, p, seed):
+    rp, col = graphs.gnp(n, p, seed)
+    r = oracle.count(rp, col, vertex=True, edge=True)
+    K = r["kmax"]
+    C, cv, ce = brute_counts(rp, col, K)
+    assert r["C"] == C
+    assert oracle.to_int(r["cv"]) == cv
+    assert oracle.to_int(r["ce"]) == ce
+
+
+def test_bruteforce_planted():
+    rp, col = graphgen.generate(40, er_avg_deg=5.0, planted=[(2, 8, 12, 1.0), (1, 10, 10, 0.8)], seed=3)
+    r = oracle.count(rp, col, vertex=True, edge=True)
+    C, cv, ce = brute_counts(rp, col, r["kmax"])
+    assert r["C"] == C and oracle.to_int(r["cv"]) == cv and oracle.to_int(r["ce"]) == ce
+
+
+# ------------------------------------------------------------ matrix identities
+
+@pytest.mark.parametrize("kind", ["gnp", "er2k"])
+def test_triangles_from_adjacency_powers(kind):
+    if kind == "gnp":
+        rp, col = graphs.gnp(300, 0.06, 11)
+    else:
+        rp, col = graphgen.workload("er2k_d20_clique30")
+    n = len(rp) - 1
+    A = np.zeros((n, n))
+    src = np.repeat(np.arange(n), np.diff(rp))
+    A[src, col.astype(np.int64)] = 1.0
+    A2 = A @ A
+    A3diag = np.einsum("ij,ji->i", A2, A)
+    r = oracle.count(rp, col, kmax=3, vertex=True, edge=True)
+    assert r["C"][3] == int(round(A3diag.sum() / 6))
+    cv = oracle.to_int(r["cv"])
+    assert [row[3] for row in cv] == [int(round(x / 2)) for x in A3diag]
+    ce = oracle.to_int(r["ce"])
+    edges = graphgen.edge_list(rp, col)
+    assert [row[3] for row in ce] == [int(round(A2[u, v])) for u, v in edges]
+
+
+def test_local_sum_identities():
+    rp, col = graphgen.generate(600, er_avg_deg=9.0, planted=[(4, 8, 20, 1.0), (2, 15, 25, 0.85)], seed=21)
+    n, m = len(rp) - 1, len(col) // 2
+    r = oracle.count(rp, col, vertex=True, edge=True)
+    C, cv, ce = r["C"], oracle.to_int(r["cv"]), oracle.to_int(r["ce"])
+    K = r["kmax"]
+    assert C[1] == n and C[2] == m
+    for k in range(K + 1):
+        assert sum(row[k] for row in cv) == k * C[k]
+        assert sum(row[k] for row in ce) == math.comb(k, 2) * C[k]
+    deg = np.diff(rp)
+    assert [row[1] for row in cv] == [1] * n
+    assert [row[2] for row in cv] == [int(d) for d in deg]
+    assert all(row[2] == 1 for row in ce)
+    omega = max(k for k in range(K + 1) if C[k])
+    assert omega <= r["alpha"] + 1
+
+
+# ------------------------------------------------------------ Thm. scr
+
+@pytest.mark.parametrize("make", [lambda: graphs.gnp(14, 0.5, 7), lambda: graphs.gnp(18, 0.65, 8),
+                                  lambda: graphs.multipartite([2, 3, 2, 2]),
+                                  lambda: graphs.complete(6), lambda: graphs.clique_minus_star(9, 2, 3)])
+def test_unique_encoding(make):
+    """Every clique is H(T) + Q for exactly one path T and Q subset of P(T)."""
+    rp, col = make()
+    adj = graphs.adjacency_sets(rp, col)
+    seen = []
+    for H, P in oracle.paths(rp, col):
+        members = H + P
+        assert len(set(members)) == len(members)
+        for a, b in itertools.combinations(members, 2):
+            assert b in adj[a], "path vertices must form a clique"
+        for k in range(len(P) + 1):
+            for Q in itertools.combinations(P, k):
+                seen.append(tuple(sorted(H + list(Q))))
+    assert len(seen) == len(set(seen)), "a clique is represented twice"
+    assert set(seen) == set(tuple(sorted(c)) for c in all_cliques(rp, col))
+
+
+# ------------------------------------------------------------ invariances
+
+def test_relabelling_invariance():
+    rp, col = graphgen.generate(300, er_avg_deg=10.0, planted=[(3, 10, 18, 1.0)], seed=4)
+    n = len(rp) - 1
+    perm = np.random.default_rng(1).permutation(n)
+    rp2, col2 = graphs.relabel(rp, col, perm)
+    a = oracle.count(rp, col, vertex=True, edge=True)
+    b = oracle.count(rp2, col2, kmax=a["kmax"], vertex=True, edge=True)
+    assert a["C"] == b["C"]
+    cva, cvb = oracle.to_int(a["cv"]), oracle.to_int(b["cv"])
+    assert all(cva[v] == cvb[perm[v]] for v in range(n))
+    ea = graphgen.edge_list(rp, col)
+    eb = {tuple(e): i for i, e in enumerate(graphgen.edge_list(rp2, col2).tolist())}
+    cea, ceb = oracle.to_int(a["ce"]), oracle.to_int(b["ce"])
+    for i, (u, v) in enumerate(ea):
+        x, y = perm[u], perm[v]
+        assert cea[i] == ceb[eb[(min(x, y), max(x, y))]]
+
+
+def test_truncation_matches_prefix():
+    rp, col = graphgen.generate(500, er_avg_deg=12.0, planted=[(2, 12, 20, 1.0)], seed=6)
+    full = oracle.count(rp, col, vertex=True, edge=True)
+    for kmax in [0, 1, 2, 3, 6]:
+        t = oracle.count(rp, col, kmax=kmax, vertex=True, edge=True)
+        assert t["C"] == full["C"][:kmax + 1]
+        assert (t["cv"] == full["cv"][:, :kmax + 1]).all()
+        assert (t["ce"] == full["ce"][:, :kmax + 1]).all()
+        assert t["nodes"] <= full["nodes"]
+
+
+def test_edge_deletion_is_monotone():
+    rp, col = graphgen.generate(200, er_avg_deg=14.0, planted=[(2, 10, 14, 1.0)], seed=8)
+    e = graphgen.edge_list(rp, col)
+    keep = np.random.default_rng(2).random(len(e)) > 0.1
+    rp2, col2 = graphgen.from_edges(len(rp) - 1, e[keep])
+    a = oracle.count(rp, col)
+    b = oracle.count(rp2, col2, kmax=a["kmax"])
+    assert all(x >= y for x, y in zip(a["C"], b["C"]))
+
+
+# ------------------------------------------------------------ degeneracy
+
+def core_numbers(row_ptr, col):
+    """k-cores by repeated deletion of vertices of degree < k (definition)."""
+    adj = graphs.adjacency_sets(row_ptr, col)
+    n = len(adj)
+    core = [0] * n
+    alive = set(range(n))
+    k = 0
+    while alive:
+        k += 1
+        changed = True
+        while changed:
+            changed = False
+            for v in list(alive):
+                if len(adj[v] & alive) < k:
+                    alive.discard(v)
+                    core[v] = k - 1
+                    changed = True
+    return core
+
+
+@pytest.mark.parametrize("make", [lambda: graphs.gnp(60, 0.2, 1), lambda: graphs.complete(9),
+                                  lambda: graphgen.generate(400, er_avg_deg=6.0, planted=[(2, 9, 15, 1.0)], seed=2)])
+def test_degeneracy_order(make):
+    rp, col = make()
+    rank, core, alpha = oracle.orient(rp, col)
+    want = core_numbers(rp, col)
+    assert list(core) == want
+    assert alpha == max(want)
+    # every vertex has at most alpha neighbours ranked after it
+    n = len(rp) - 1
+    for v in range(n):
+        nb = col[rp[v]:rp[v + 1]]
+        assert (rank[nb] > rank[v]).sum() <= alpha
+
+
+def test_limb_overflow_is_reported():
+    rp, col = graphs.complete(40)  # C(40,20) > 2^32
+    with pytest.raises(RuntimeError, match="overflow"):
+        oracle.count(rp, col, nl=1)
+    assert oracle.count(rp, col, nl=2)["C"][20] == math.comb(40, 20)
