@@ -1,0 +1,156 @@
+/*
+ * pivoter.h -- C ABI of libpivoter: exact k-clique counts for every k, on one
+ * GPU, with the Succinct Clique Tree (SCT) of Jain & Seshadhri, "The Power of
+ * Pivoting for Exact Clique Counting" (WSDM 2020).
+ *
+ * Conventions shared by every entry point
+ *   - Graphs are given as CSR over vertices 0..n-1: row_ptr int64[n+1] and
+ *     col uint32[nnz] with nnz = row_ptr[n] = 2m.  The graph must be simple
+ *     and undirected (Sec. 3.1, "Problem Statement"; Sec. 3.2): every row is
+ *     sorted strictly ascending, no self-loops, and v is in row u exactly
+ *     when u is in row v.  Directed inputs must be symmetrised by the caller
+ *     (the paper ignores edge directions, Sec. 5).
+ *   - "device" pointers are CUDA global-memory pointers on the current
+ *     device; "host" pointers are ordinary CPU memory.  The caller owns every
+ *     buffer it passes in; the library owns the pvt_dag and its scratch.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Calls return once their results are complete and checked.
+ *   - Counts are exact unsigned integers of W little-endian 64-bit words
+ *     (word 0 least significant).  Arrays are indexed [.. ][k][word] with
+ *     k = 0..kmax the clique size: entry 0 is 0, k = 1 counts vertices, k = 2
+ *     edges, and entries with k above the clique number are 0.
+ *   - Edge ids: edge {u, v} has the id of (min, max) in lexicographic order,
+ *     i.e. its rank in the upper triangle of the CSR read row by row.
+ *   - No C++ exception crosses the ABI.  On failure a call returns a status
+ *     other than PVT_OK, leaves output buffers unspecified, and
+ *     pvt_last_error() returns a message for the calling thread.
+ */
+#ifndef PIVOTER_H
+#define PIVOTER_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum pvt_status {
+    PVT_OK = 0,
+    PVT_EINVAL = 1,      /* bad argument (sizes, NULL pointers, kmax) */
+    PVT_ENOTSIMPLE = 2,  /* CSR not sorted / symmetric / loop-free (with PVT_VALIDATE) */
+    PVT_ENOMEM = 3,      /* device allocation failed */
+    PVT_EOVERFLOW = 4,   /* W words cannot hold every count of this graph */
+    PVT_ECUDA = 5,       /* a CUDA call failed */
+    PVT_ETIMEOUT = 6,    /* a bounded device-side wait expired */
+    PVT_EINTERNAL = 7    /* a device-side capacity check failed (a library bug) */
+} pvt_status;
+
+/* Opaque, library-owned device state of one oriented graph. */
+typedef struct pvt_dag pvt_dag;
+
+/* pvt_orient flags: check that the CSR is a simple undirected graph first;
+ * time every phase with CUDA events from the start (see pvt_dag_stats). */
+#define PVT_VALIDATE 0x1u
+#define PVT_PROFILE 0x2u
+
+/*
+ * Orient the graph along a degeneracy order (Lemma degen, Sec. 3.2; Alg. 1
+ * step 1): k-core peeling on the device, then the out-neighbourhoods N+(v)
+ * as a CSR over the DAG, every out-degree at most the degeneracy alpha.
+ *   n, nnz       vertex count (< 2^32) and row_ptr[n] (= 2m), host values
+ *   row_ptr,col  device CSR as above.  It is borrowed, not copied: it must
+ *                stay valid and unchanged until pvt_dag_free (per-edge counts
+ *                read it again).
+ *   flags        0, PVT_VALIDATE (else the CSR is trusted), PVT_PROFILE
+ *   dag_out      receives the new pvt_dag (host pointer to a pointer)
+ *   alpha_out    receives the largest out-degree (host; may be NULL)
+ * Errors: PVT_EINVAL, PVT_ENOTSIMPLE, PVT_ENOMEM, PVT_ECUDA, PVT_ETIMEOUT.
+ */
+pvt_status pvt_orient(int64_t n, int64_t nnz, const int64_t *row_ptr, const uint32_t *col,
+                      uint32_t flags, void *stream, pvt_dag **dag_out, int32_t *alpha_out);
+
+/*
+ * Sizes of an oriented graph, all host outputs (any may be NULL): n, m,
+ * alpha, and min_words = the smallest W every count call accepts,
+ * ceil((bits(n) + alpha + 1) / 64) with a floor of 1: every clique lies in
+ * {r} + N+(r) for its first vertex r, so each count is at most n * 2^alpha.
+ */
+pvt_status pvt_dag_info(const pvt_dag *dag, int64_t *n, int64_t *m, int32_t *alpha,
+                        int32_t *min_words);
+
+/*
+ * Global counts C_k for k = 0..kmax (Sec. 3.1; Alg. 2, the C_{|H|+i} update;
+ * correctness: proof of Thm. main).  Each root vertex r explores the SCT
+ * below its child N+(r) (Alg. 1) depth first; every root-to-leaf path T with
+ * h = |H(T)| and p = |P(T)| adds C(p, i) to C_{h+i}.  kmax truncates (Sec. 4,
+ * "Counting k-cliques for a specific k"): branches with more than kmax hold
+ * links are cut and the counts for k <= kmax stay exact.
+ *   kmax   >= 0; any value is accepted (entries above the clique number are 0)
+ *   W      words per count, >= min_words (else PVT_EOVERFLOW before any launch)
+ *   C      device uint64[kmax+1][W], written in full
+ * Errors: PVT_EINVAL, PVT_EOVERFLOW, PVT_ENOMEM, PVT_ECUDA, PVT_EINTERNAL.
+ */
+pvt_status pvt_count_global(pvt_dag *dag, int32_t kmax, int32_t W, uint64_t *C, void *stream);
+
+/*
+ * Per-vertex counts c_k(v) (Sec. 3.1; Alg. 2 steps ht and pt): for each path
+ * T, every v in H(T) gains C(p, i) at k = h+i and every v in P(T) gains
+ * C(p-1, i) at k = h+1+i.  The paper leaves parallel local counts as future
+ * work (Sec. 4, "Parallel version"); here roots run in parallel and add into
+ * one table with exact carry-propagating atomics.
+ *   cv     device uint64[n][kmax+1][W], written in full
+ * Other arguments and errors as pvt_count_global.
+ */
+pvt_status pvt_count_local_vertex(pvt_dag *dag, int32_t kmax, int32_t W, uint64_t *cv,
+                                  void *stream);
+
+/*
+ * Per-edge counts c_k(e) (Sec. 3.1; Alg. 2 steps hht, pht, ppt): each pair
+ * inside H(T) gains C(p, i) at k = h+i, each pair (P, H) gains C(p-1, i) at
+ * k = h+1+i and each pair inside P(T) gains C(p-2, i) at k = h+2+i.
+ *   ce     device uint64[m][kmax+1][W] indexed by edge id, written in full
+ * Other arguments and errors as pvt_count_global.
+ */
+pvt_status pvt_count_local_edge(pvt_dag *dag, int32_t kmax, int32_t W, uint64_t *ce,
+                                void *stream);
+
+/*
+ * Statistics of the last orient or count call on a dag (no counterpart in
+ * the paper's algorithms; its Fig. treesize reports SCT sizes).  Tree
+ * figures are of the walk the device performed: nodes popped from the DFS
+ * stacks (leaves included; a node whose label is a clique is closed as one
+ * leaf), root-to-leaf paths, and the bitset words ANDed and popcounted in
+ * pivot selection (|S| * ceil(d/32) per internal node).  ms[] holds device
+ * time per phase when profiling is on (else zeros): [0] peel, [1] orient
+ * (DAG CSR and root classes), [2..6] the walk kernels of out-degree classes
+ * <=32, <=64, <=128, <=256, <=512, [7] combine/finish.  Phases of different
+ * classes overlap in time.
+ */
+typedef struct pvt_stats {
+    uint64_t sct_nodes;
+    uint64_t sct_leaves;
+    uint64_t pivot_words;
+    uint64_t launches;      /* kernels launched by the call */
+    uint64_t roots[6];      /* roots per out-degree class (0, <=32, ..., <=512) */
+    uint64_t class_words[6];/* pivot_words split by out-degree class */
+    float ms[8];
+} pvt_stats;
+
+/* Copy the statistics of the last call into *out (host). */
+pvt_status pvt_dag_stats(const pvt_dag *dag, pvt_stats *out);
+
+/* Enable (1) or disable (0) per-phase device timing with CUDA events. */
+pvt_status pvt_dag_set_profiling(pvt_dag *dag, int32_t enable);
+
+/* Release a pvt_dag and all its device memory (NULL is ignored). */
+void pvt_dag_free(pvt_dag *dag);
+
+/* Message for the last failed call on this thread ("" if none). */
+const char *pvt_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PIVOTER_H */

@@ -1,0 +1,157 @@
+"""Exact k-clique counts for every k on one GPU, with the Succinct Clique Tree
+of Jain & Seshadhri, "The Power of Pivoting for Exact Clique Counting"
+(WSDM 2020).
+
+Thin binding over the C ABI of ``libpivoter.so`` (``include/pivoter.h``):
+PyTorch supplies device memory and streams; every step of the computation
+runs in the library's CUDA kernels.  There is no CPU fallback: without the
+built library every entry point raises ImportError.
+
+    import torch, paper_2001_06784_gb300 as pvt
+    dag = pvt.orient(row_ptr.cuda(), col.cuda())      # degeneracy DAG
+    C = pvt.to_ints(dag.count_global())               # C[k], k = 0..alpha+1
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+import torch
+
+from . import _lib
+from ._lib import PVT_PROFILE, PVT_VALIDATE, PivoterError
+
+__all__ = ["orient", "Dag", "to_ints", "count_global_host", "PivoterError"]
+
+
+def _stream_handle(stream, device):
+    s = stream if stream is not None else torch.cuda.current_stream(device)
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+class Dag:
+    """A graph oriented along its degeneracy order, resident on the GPU.
+
+    The CSR tensors it was built from are borrowed (kept alive here) and
+    must not be modified while the Dag exists."""
+
+    def __init__(self, handle, row_ptr, col):
+        self._h = handle
+        self._keep = (row_ptr, col)
+        self.device = row_ptr.device
+        n, m = ctypes.c_int64(), ctypes.c_int64()
+        a, w = ctypes.c_int32(), ctypes.c_int32()
+        _lib.check(_lib.lib().pvt_dag_info(self._h, ctypes.byref(n), ctypes.byref(m),
+                                           ctypes.byref(a), ctypes.byref(w)))
+        self.n, self.m, self.alpha, self.min_words = n.value, m.value, a.value, w.value
+
+    def _args(self, kmax, W):
+        kmax = self.alpha + 1 if kmax is None else int(kmax)
+        W = self.min_words if W is None else int(W)
+        return kmax, W
+
+    def _out(self, rows, kmax, W, out):
+        shape = (rows, kmax + 1, W) if rows is not None else (kmax + 1, W)
+        if out is None:
+            return torch.empty(shape, dtype=torch.int64, device=self.device)
+        if out.dtype != torch.int64 or tuple(out.shape) != shape or not out.is_contiguous():
+            raise ValueError(f"out must be a contiguous int64 tensor of shape {shape}")
+        return out
+
+    def count_global(self, kmax=None, W=None, out=None, stream=None):
+        """C_k for k = 0..kmax as an int64 tensor [kmax+1, W] of 64-bit words
+        (little-endian, reinterpret as unsigned)."""
+        kmax, W = self._args(kmax, W)
+        out = self._out(None, kmax, W, out)
+        _lib.check(_lib.lib().pvt_count_global(self._h, kmax, W, ctypes.c_void_p(out.data_ptr()),
+                                               _stream_handle(stream, self.device)))
+        return out
+
+    def count_local_vertex(self, kmax=None, W=None, out=None, stream=None):
+        """c_k(v) as an int64 tensor [n, kmax+1, W]."""
+        kmax, W = self._args(kmax, W)
+        out = self._out(self.n, kmax, W, out)
+        _lib.check(_lib.lib().pvt_count_local_vertex(self._h, kmax, W, ctypes.c_void_p(out.data_ptr()),
+                                                     _stream_handle(stream, self.device)))
+        return out
+
+    def count_local_edge(self, kmax=None, W=None, out=None, stream=None):
+        """c_k(e) as an int64 tensor [m, kmax+1, W], rows in edge-id order
+        (lexicographic (min, max))."""
+        kmax, W = self._args(kmax, W)
+        out = self._out(self.m, kmax, W, out)
+        _lib.check(_lib.lib().pvt_count_local_edge(self._h, kmax, W, ctypes.c_void_p(out.data_ptr()),
+                                                   _stream_handle(stream, self.device)))
+        return out
+
+    PHASES = ("peel", "orient", "walk_d32", "walk_d64", "walk_d128", "walk_d256", "walk_d512", "finish")
+
+    def stats(self):
+        """Statistics of the last call on this dag (see pvt_stats): SCT walk
+        sizes, kernel launches, roots per out-degree class and, when
+        profiling is on, device milliseconds per phase."""
+        st = _lib.Stats()
+        _lib.check(_lib.lib().pvt_dag_stats(self._h, ctypes.byref(st)))
+        return dict(sct_nodes=st.sct_nodes, sct_leaves=st.sct_leaves, pivot_words=st.pivot_words,
+                    launches=st.launches, roots=list(st.roots), class_words=list(st.class_words),
+                    ms=dict(zip(self.PHASES, list(st.ms))))
+
+    def set_profiling(self, on: bool):
+        _lib.check(_lib.lib().pvt_dag_set_profiling(self._h, 1 if on else 0))
+
+    def free(self):
+        if self._h:
+            _lib.lib().pvt_dag_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def orient(row_ptr: torch.Tensor, col: torch.Tensor, *, validate: bool = False, profile: bool = False,
+           stream=None) -> Dag:
+    """Orient a CSR graph (device tensors: row_ptr int64[n+1], col int32 or
+    uint32 [2m]) along a degeneracy order on the GPU."""
+    if not (row_ptr.is_cuda and col.is_cuda):
+        raise ValueError("row_ptr and col must be CUDA tensors")
+    if row_ptr.dtype != torch.int64 or col.dtype not in (torch.int32, torch.uint32):
+        raise ValueError("row_ptr must be int64 and col int32/uint32")
+    row_ptr = row_ptr.contiguous()
+    col = col.contiguous()
+    n = row_ptr.numel() - 1
+    nnz = col.numel()
+    h = ctypes.c_void_p()
+    alpha = ctypes.c_int32()
+    with torch.cuda.device(row_ptr.device):
+        _lib.check(_lib.lib().pvt_orient(n, nnz, ctypes.c_void_p(row_ptr.data_ptr()),
+                                         ctypes.c_void_p(col.data_ptr() if nnz else 0),
+                                         (PVT_VALIDATE if validate else 0) | (PVT_PROFILE if profile else 0),
+                                         _stream_handle(stream, row_ptr.device), ctypes.byref(h),
+                                         ctypes.byref(alpha)))
+    return Dag(h, row_ptr, col)
+
+
+def to_ints(t):
+    """Word tensor [..., W] (64-bit little-endian words) -> nested lists of
+    Python ints."""
+    a = t.detach().cpu().numpy().view(np.uint64) if isinstance(t, torch.Tensor) else np.asarray(t, np.uint64)
+    if a.ndim == 1:
+        v = 0
+        for x in a[::-1]:
+            v = (v << 64) | int(x)
+        return v
+    return [to_ints(x) for x in a]
+
+
+def count_global_host(row_ptr, col, kmax=None, device="cuda"):
+    """End-to-end convenience: host CSR (numpy) in, C_k as Python ints out."""
+    rp = torch.as_tensor(np.asarray(row_ptr, dtype=np.int64)).to(device)
+    cl = torch.as_tensor(np.asarray(col, dtype=np.uint32).view(np.int32)).to(device)
+    dag = orient(rp, cl)
+    try:
+        return to_ints(dag.count_global(kmax))
+    finally:
+        dag.free()

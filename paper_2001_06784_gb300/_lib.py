@@ -1,0 +1,79 @@
+"""ctypes declarations of libpivoter's C ABI (include/pivoter.h).
+
+Argument marshalling only.  The library is the in-tree ``libpivoter.so``;
+there is no fallback: importing this module without it raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libpivoter.so")
+
+STATUS = {
+    0: "PVT_OK", 1: "PVT_EINVAL", 2: "PVT_ENOTSIMPLE", 3: "PVT_ENOMEM", 4: "PVT_EOVERFLOW",
+    5: "PVT_ECUDA", 6: "PVT_ETIMEOUT", 7: "PVT_EINTERNAL",
+}
+PVT_VALIDATE = 0x1
+PVT_PROFILE = 0x2
+
+
+class Stats(ctypes.Structure):
+    """pvt_stats (include/pivoter.h)."""
+    _fields_ = [("sct_nodes", ctypes.c_uint64), ("sct_leaves", ctypes.c_uint64),
+                ("pivot_words", ctypes.c_uint64), ("launches", ctypes.c_uint64),
+                ("roots", ctypes.c_uint64 * 6), ("class_words", ctypes.c_uint64 * 6),
+                ("ms", ctypes.c_float * 8)]
+
+# every symbol include/pivoter.h declares
+EXPORTS = ("pvt_orient", "pvt_dag_info", "pvt_count_global", "pvt_count_local_vertex",
+           "pvt_count_local_edge", "pvt_dag_stats", "pvt_dag_set_profiling", "pvt_dag_free",
+           "pvt_last_error")
+
+
+class PivoterError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS.get(status, status)}: {message}")
+        self.status = status
+
+
+def load(path: str = LIB_PATH):
+    if not os.path.exists(path):
+        raise ImportError(f"libpivoter.so not built at {path}; run __graft_entry__.build()")
+    lib = ctypes.CDLL(path)
+    vp, i64, i32, u32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_uint32
+    lib.pvt_orient.restype = i32
+    lib.pvt_orient.argtypes = [i64, i64, vp, vp, u32, vp, ctypes.POINTER(vp), ctypes.POINTER(i32)]
+    lib.pvt_dag_info.restype = i32
+    lib.pvt_dag_info.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(i32),
+                                 ctypes.POINTER(i32)]
+    for fn in ("pvt_count_global", "pvt_count_local_vertex", "pvt_count_local_edge"):
+        f = getattr(lib, fn)
+        f.restype = i32
+        f.argtypes = [vp, i32, i32, vp, vp]
+    lib.pvt_dag_stats.restype = i32
+    lib.pvt_dag_stats.argtypes = [vp, ctypes.POINTER(Stats)]
+    lib.pvt_dag_set_profiling.restype = i32
+    lib.pvt_dag_set_profiling.argtypes = [vp, i32]
+    lib.pvt_dag_free.restype = None
+    lib.pvt_dag_free.argtypes = [vp]
+    lib.pvt_last_error.restype = ctypes.c_char_p
+    lib.pvt_last_error.argtypes = []
+    return lib
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = load()
+    return _lib
+
+
+def check(status: int):
+    if status != 0:
+        msg = lib().pvt_last_error().decode(errors="replace")
+        raise PivoterError(status, msg)

@@ -1,0 +1,754 @@
+// SCT walk and clique counts on the device.
+//
+// For every root r (a child N+(r) of the SCT's root, Alg. 1 step 3) one warp
+//   1. gathers the subgraph induced on N+(r) into a shared-memory bitset
+//      adjacency: member i = the i-th out-neighbour of r (ascending id); for
+//      every member u it scans N+(u) and sets bits i<->j for the members it
+//      finds.  Edges among members are undirected (N(S,u) = N(u) cap S,
+//      Sec. 3.2), and each appears in exactly one of the two out-lists.
+//   2. walks the SCT below N+(r) depth first with an explicit stack of
+//      frames (S as a bitset, h, p) (Sec. 4, "Storage cost"): at a node S the
+//      pivot is the member of S with most neighbours in S (Alg. 1 pivot step;
+//      ties: lowest member index), the pivot child is N(S,p) with p+1, and the
+//      non-neighbours v_1 < ... < v_l of the pivot give hold children
+//      N(S,v_i) \ {v_1..v_{i-1}} with h+1 (Alg. 1 hold step).  A node whose S
+//      is a clique has a single root-to-leaf continuation (every further
+//      pivot is adjacent to all of S), so it is closed at once as a leaf with
+//      p + |S| pivot links.  At most d+1 frames are ever live: a node of size
+//      s with l non-neighbours pushes l+1 children, each of size <= s-1-l.
+//   3. tallies every leaf (h = |H(T)|, p = |P(T)|, Alg. 2):
+//        global  : a 64-bit histogram over (h, p); the counts
+//                  C_k = sum hist[h][p] * C(p, k-h) are combined at the end
+//                  in exact multi-word arithmetic (proof of Thm. main);
+//        vertex  : Alg. 2 steps ht/pt into the caller's table;
+//        edge    : Alg. 2 steps hht/pht/ppt into the caller's table;
+//      both local forms add multi-word binomials with carry-propagating
+//      64-bit atomics, so results are exact whatever the order.
+// Roots come from a device work queue (persistent warps) in descending
+// out-degree, one kernel instance per bitset width NW = ceil(d / 32).
+#include <algorithm>
+
+#include "pvt_internal.cuh"
+
+namespace pvt {
+
+enum Mode { MODE_GLOBAL = 0, MODE_VERTEX = 1, MODE_EDGE = 2 };
+
+template <int NW>
+struct WarpWork {
+    static constexpr int D = 32 * NW;                // largest out-degree handled
+    static constexpr int RS = NW == 1 ? 1 : NW + 1;  // odd row stride: no bank conflicts
+    int64_t rs[D];               // start of N+(member) in ocol
+    uint32_t ids[D];             // member vertex ids (ascending)
+    uint32_t off[D + 1];         // prefix sums of |N+(member)|
+    uint32_t adj[D * RS];        // adjacency bitset rows
+    uint32_t stk[(D + 1) * NW];  // DFS stack: S bitsets
+    uint32_t hp[D + 1];          // DFS stack: (h << 16) | p
+    uint16_t lk[D + 1];          // DFS stack: link into the frame (local modes)
+    uint16_t path[D + 2];        // link label at each depth of the current path
+    uint16_t memH[D + 2];        // leaf members: hold vertices (local index, d = root)
+    uint16_t memP[D + 2];        // leaf members: pivot vertices
+};
+
+constexpr uint16_t LINK_PIVOT = 0x8000u;
+
+// --------------------------------------------------- multi-word atomics
+
+// a[0..W) += x (one word), carries propagated with further atomics.
+__device__ __forceinline__ void atomic_add_u64_carry(unsigned long long *a, unsigned long long x,
+                                                     int W, unsigned *err)
+{
+    unsigned long long old = atomicAdd(a, x);
+    if (old + x >= old) return;
+    for (int j = 1; j < W; ++j) {
+        old = atomicAdd(a + j, 1ull);
+        if (old != ~0ull) return;
+    }
+    atomicOr(err, DERR_OVERFLOW);
+}
+
+// a[0..W) += b[0..W) as one multi-word integer.
+__device__ __forceinline__ void atomic_add_multi(unsigned long long *a,
+                                                 const unsigned long long *__restrict__ b, int W,
+                                                 unsigned *err)
+{
+    unsigned long long c = 0;
+    for (int j = 0; j < W; ++j) {
+        unsigned long long bj = b[j];
+        if (bj == 0 && c == 0) continue;
+        unsigned long long add = bj + c;
+        unsigned long long c2 = (add < bj) ? 1ull : 0ull;  // bj = ~0 and c = 1
+        unsigned long long old = add ? atomicAdd(a + j, add) : 0ull;
+        c = c2 + ((old + add < old) ? 1ull : 0ull);
+    }
+    if (c) atomicOr(err, DERR_OVERFLOW);
+}
+
+__device__ __forceinline__ const unsigned long long *binom_at(const unsigned long long *B, int a,
+                                                              int b, int W)
+{
+    return B + ((size_t)a * (a + 1) / 2 + b) * W;
+}
+
+// ------------------------------------------------------- leaf tallies
+
+struct CountArgs {
+    const int64_t *orow;
+    const uint32_t *ocol;
+    const uint32_t *oeid;
+    const uint32_t *roots;
+    unsigned nroots;
+    unsigned *qhead;
+    unsigned long long *hist;   // global mode: (h, p) histogram, row stride hstride
+    int hstride;
+    unsigned long long *out;    // local modes: [count][K][W]
+    const unsigned long long *B;  // multi-word Pascal table
+    int W;
+    int kmax;
+    unsigned *err;
+    unsigned long long *stats;  // [0] nodes, [1] leaves, [2] pivot words, [3 + class] words
+    int cls;                    // out-degree class of the launch
+};
+
+struct WalkCounters {
+    unsigned long long nodes = 0, leaves = 0, words = 0;
+};
+
+// Edge id of the edge between members a and b (local indices, d = root).
+template <int NW>
+__device__ __forceinline__ uint32_t member_edge_id(const WarpWork<NW> &Wk, const CountArgs &A,
+                                                   int64_t rbeg, int d, int a, int b)
+{
+    if (a == d) return A.oeid[rbeg + b];
+    if (b == d) return A.oeid[rbeg + a];
+    // the edge sits in exactly one of N+(u_a), N+(u_b): search both
+    for (int t = 0; t < 2; ++t) {
+        int x = t ? b : a, y = t ? a : b;
+        int64_t lo = Wk.rs[x], hi = lo + (Wk.off[x + 1] - Wk.off[x]);
+        uint32_t key = Wk.ids[y];
+        while (lo < hi) {
+            int64_t mid = lo + ((hi - lo) >> 1);
+            if (A.ocol[mid] < key) lo = mid + 1; else hi = mid;
+        }
+        if (lo < Wk.rs[x] + (Wk.off[x + 1] - Wk.off[x]) && A.ocol[lo] == key) return A.oeid[lo];
+    }
+    atomicOr(A.err, DERR_RANGE);
+    return 0xFFFFFFFFu;
+}
+
+// Adds C(a, i) at k = s + i (i = 0..a, k <= kmax) to row `cell` ([K][W]).
+__device__ __forceinline__ void add_binom_row(unsigned long long *cell, int s, int a,
+                                              const CountArgs &A)
+{
+    for (int i = 0; i <= a; ++i) {
+        int k = s + i;
+        if (k > A.kmax) break;
+        atomic_add_multi(cell + (size_t)k * A.W, binom_at(A.B, a, i, A.W), A.W, A.err);
+    }
+}
+
+// Leaf of a local-count walk: path links at depths 1..t, plus the clique X
+// (as extra pivot links) when the leaf closes a clique node.
+template <int NW, int MODE>
+__device__ void local_leaf(WarpWork<NW> &Wk, const CountArgs &A, int lane, uint32_t r, int64_t rbeg,
+                           int d, int h, int p, int t, const uint32_t *X)
+{
+    constexpr int D = WarpWork<NW>::D;
+    // members: H = root + hold links, P = pivot links + X
+    int nh = 0, np = 0;
+    if (lane == 0) Wk.memH[0] = (uint16_t)d;
+    nh = 1;
+    for (int base = 1; base <= t; base += 32) {
+        int j = base + lane;
+        uint16_t l = j <= t ? Wk.path[j] : 0;
+        bool valid = j <= t;
+        bool piv = valid && (l & LINK_PIVOT);
+        bool hold = valid && !(l & LINK_PIVOT);
+        unsigned bh = __ballot_sync(FULL, hold), bp = __ballot_sync(FULL, piv);
+        unsigned below = (1u << lane) - 1u;
+        if (hold) Wk.memH[nh + __popc(bh & below)] = (uint16_t)(l & 0x7FFF);
+        if (piv) Wk.memP[np + __popc(bp & below)] = (uint16_t)(l & 0x7FFF);
+        nh += __popc(bh);
+        np += __popc(bp);
+    }
+    if (X) {
+#pragma unroll
+        for (int w = 0; w < NW; ++w) {
+            bool in = (X[w] >> lane) & 1u;
+            unsigned bx = __ballot_sync(FULL, in);
+            if (in) Wk.memP[np + __popc(bx & ((1u << lane) - 1u))] = (uint16_t)(w * 32 + lane);
+            np += __popc(bx);
+        }
+    }
+    __syncwarp();
+    if (nh != h || np != p || nh + np > D + 1) {
+        if (lane == 0) atomicOr(A.err, DERR_RANGE);
+        return;
+    }
+    auto gid = [&](int loc) -> uint32_t { return loc == d ? r : Wk.ids[loc]; };
+    if (MODE == MODE_VERTEX) {
+        // Alg. 2 step ht: v in H gains C(p, i) at h+i; step pt: v in P gains C(p-1, i) at h+1+i
+        for (int q = lane; q < h + p; q += 32) {
+            bool inH = q < h;
+            uint32_t v = gid(inH ? Wk.memH[q] : Wk.memP[q - h]);
+            unsigned long long *cell = A.out + (size_t)v * (A.kmax + 1) * A.W;
+            if (inH) add_binom_row(cell, h, p, A);
+            else add_binom_row(cell, h + 1, p - 1, A);
+        }
+    } else {
+        // Alg. 2 steps hht / pht / ppt over unordered member pairs
+        const int L = h + p;
+        for (int a = 0; a < L - 1; ++a) {
+            for (int b = a + 1 + lane; b < L; b += 32) {
+                int la = a < h ? Wk.memH[a] : Wk.memP[a - h];
+                int lb = b < h ? Wk.memH[b] : Wk.memP[b - h];
+                uint32_t e = member_edge_id(Wk, A, rbeg, d, la, lb);
+                if (e == 0xFFFFFFFFu) continue;
+                unsigned long long *cell = A.out + (size_t)e * (A.kmax + 1) * A.W;
+                int npiv = (a >= h) + (b >= h);
+                add_binom_row(cell, h + npiv, p - npiv, A);
+            }
+        }
+    }
+    __syncwarp();
+}
+
+// ---------------------------------------------------------- one root
+
+template <int NW, int MODE, bool SHIST>
+__device__ void walk_root(WarpWork<NW> &Wk, unsigned long long *shist, const CountArgs &A, int lane,
+                          uint32_t r, WalkCounters &wc)
+{
+    constexpr int D = WarpWork<NW>::D;
+    constexpr int RS = WarpWork<NW>::RS;
+    constexpr bool REG = NW <= 4;  // keep this lane's adjacency rows in registers
+    const int64_t rbeg = A.orow[r];
+    const int d = (int)(A.orow[r + 1] - rbeg);
+    if (d > D) {
+        if (lane == 0) atomicOr(A.err, DERR_RANGE);
+        return;
+    }
+
+    // ---- 1. gather: member ids, their out-list extents, bitset adjacency
+    uint32_t base = 0;
+#pragma unroll
+    for (int c = 0; c < NW; ++c) {
+        int i = c * 32 + lane;
+        uint32_t id = 0xFFFFFFFFu, od = 0;
+        int64_t rs = 0;
+        if (i < d) {
+            id = A.ocol[rbeg + i];
+            rs = A.orow[id];
+            od = (uint32_t)(A.orow[id + 1] - rs);
+        }
+        uint32_t inc = od;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t t = __shfl_up_sync(FULL, inc, o);
+            if (lane >= o) inc += t;
+        }
+        Wk.ids[i] = id;
+        Wk.rs[i] = rs;
+        Wk.off[i + 1] = base + inc;
+        base += __shfl_sync(FULL, inc, 31);
+    }
+    if (lane == 0) Wk.off[0] = 0;
+    for (int t = lane; t < d * RS; t += 32) Wk.adj[t] = 0;
+    __syncwarp();
+    const uint32_t T = base;
+    for (uint32_t t = lane; t < T; t += 32) {
+        int lo = 0, hi = d - 1;  // largest i with off[i] <= t
+        while (lo < hi) {
+            int mid = (lo + hi + 1) >> 1;
+            if (Wk.off[mid] <= t) lo = mid; else hi = mid - 1;
+        }
+        uint32_t x = A.ocol[Wk.rs[lo] + (t - Wk.off[lo])];
+        int a = 0, b = d;
+        while (a < b) {
+            int mid = (a + b) >> 1;
+            if (Wk.ids[mid] < x) a = mid + 1; else b = mid;
+        }
+        if (a < d && Wk.ids[a] == x) {
+            atomicOr(&Wk.adj[lo * RS + (a >> 5)], 1u << (a & 31));
+            atomicOr(&Wk.adj[a * RS + (lo >> 5)], 1u << (lo & 31));
+        }
+    }
+    __syncwarp();
+
+    uint32_t myrow[REG ? NW : 1][REG ? NW : 1];
+    if (REG) {
+#pragma unroll
+        for (int j = 0; j < NW; ++j)
+#pragma unroll
+            for (int w = 0; w < NW; ++w) {
+                int i = j * 32 + lane;
+                myrow[j % (REG ? NW : 1)][w % (REG ? NW : 1)] = i < d ? Wk.adj[i * RS + w] : 0u;
+            }
+    }
+    auto row = [&](int j, int w) -> uint32_t {
+        if (REG) return myrow[j % (REG ? NW : 1)][w % (REG ? NW : 1)];
+        return Wk.adj[(j * 32 + lane) * RS + w];
+    };
+
+    // ---- 2. depth-first walk
+    if (lane == 0) {
+#pragma unroll
+        for (int w = 0; w < NW; ++w) {
+            int bits = d - 32 * w;
+            Wk.stk[w] = bits >= 32 ? FULL : (bits <= 0 ? 0u : ((1u << bits) - 1u));
+        }
+        Wk.hp[0] = (1u << 16);
+        if (MODE != MODE_GLOBAL) { Wk.lk[0] = 0; Wk.path[0] = (uint16_t)d; }
+    }
+    int top = 1;
+    __syncwarp();
+    while (top > 0) {
+        --top;
+        uint32_t S[NW];
+#pragma unroll
+        for (int w = 0; w < NW; ++w) S[w] = Wk.stk[top * NW + w];
+        const uint32_t hp = Wk.hp[top];
+        const int h = (int)(hp >> 16), p = (int)(hp & 0xFFFFu);
+        const int depth = h + p - 1;
+        if (MODE != MODE_GLOBAL) {
+            uint16_t l = Wk.lk[top];
+            __syncwarp();
+            if (lane == 0 && depth > 0) Wk.path[depth] = l;
+            __syncwarp();
+        }
+        int s = 0;
+#pragma unroll
+        for (int w = 0; w < NW; ++w) s += __popc(S[w]);
+        wc.nodes++;
+        if (s == 0) {
+            wc.leaves++;
+            if (MODE == MODE_GLOBAL) {
+                if (lane == 0) {
+                    if (SHIST) atomicAdd(&shist[h * (D + 1) + p], 1ull);
+                    else atomicAdd(&A.hist[(size_t)h * A.hstride + p], 1ull);
+                }
+            } else {
+                local_leaf<NW, MODE>(Wk, A, lane, r, rbeg, d, h, p, depth, nullptr);
+            }
+            __syncwarp();
+            continue;
+        }
+        // pivot: most neighbours inside S, ties -> lowest member index
+        uint32_t best = 0;
+#pragma unroll
+        for (int j = 0; j < NW; ++j) {
+            if ((S[j] >> lane) & 1u) {
+                uint32_t c = 0;
+#pragma unroll
+                for (int w = 0; w < NW; ++w) c += __popc(row(j, w) & S[w]);
+                uint32_t key = ((c + 1u) << 10) | (1023u - (uint32_t)(j * 32 + lane));
+                best = max(best, key);
+            }
+        }
+        best = __reduce_max_sync(FULL, best);
+        wc.words += (unsigned long long)s * NW;
+        const int piv = 1023 - (int)(best & 1023u);
+        const int cmax = (int)(best >> 10) - 1;
+        if (cmax == s - 1) {
+            // S is a clique: one leaf with |S| more pivot links
+            wc.leaves++;
+            if (MODE == MODE_GLOBAL) {
+                if (lane == 0) {
+                    if (SHIST) atomicAdd(&shist[h * (D + 1) + p + s], 1ull);
+                    else atomicAdd(&A.hist[(size_t)h * A.hstride + p + s], 1ull);
+                }
+            } else {
+                local_leaf<NW, MODE>(Wk, A, lane, r, rbeg, d, h, p + s, depth, S);
+            }
+            __syncwarp();
+            continue;
+        }
+        uint32_t R[NW];
+        int nR = 0;
+#pragma unroll
+        for (int w = 0; w < NW; ++w) {
+            R[w] = S[w] & ~Wk.adj[piv * RS + w];
+            if (w == (piv >> 5)) R[w] &= ~(1u << (piv & 31));
+            nR += __popc(R[w]);
+        }
+        const bool hold_ok = h + 1 <= A.kmax;
+        const int npush = 1 + (hold_ok ? nR : 0);
+        if (top + npush > D + 1) {
+            if (lane == 0) atomicOr(A.err, DERR_STACK);
+            return;
+        }
+        __syncwarp();  // every lane has read frame `top`
+        if (lane == 0) {
+#pragma unroll
+            for (int w = 0; w < NW; ++w) Wk.stk[top * NW + w] = Wk.adj[piv * RS + w] & S[w];
+            Wk.hp[top] = ((uint32_t)h << 16) | (uint32_t)(p + 1);
+            if (MODE != MODE_GLOBAL) Wk.lk[top] = (uint16_t)(LINK_PIVOT | piv);
+        }
+        if (hold_ok) {
+            int before = 0;
+#pragma unroll
+            for (int j = 0; j < NW; ++j) {
+                if ((R[j] >> lane) & 1u) {
+                    const uint32_t low = (1u << lane) - 1u;
+                    const int f = top + 1 + before + __popc(R[j] & low);
+#pragma unroll
+                    for (int w = 0; w < NW; ++w) {
+                        uint32_t below = w < j ? R[w] : (w == j ? (R[j] & low) : 0u);
+                        Wk.stk[f * NW + w] = row(j, w) & S[w] & ~below;
+                    }
+                    Wk.hp[f] = ((uint32_t)(h + 1) << 16) | (uint32_t)p;
+                    if (MODE != MODE_GLOBAL) Wk.lk[f] = (uint16_t)(j * 32 + lane);
+                }
+                before += __popc(R[j]);
+            }
+        }
+        top += npush;
+        __syncwarp();
+    }
+}
+
+template <int NW>
+constexpr int warps_per_block()
+{
+    return NW <= 2 ? 8 : (NW <= 8 ? 4 : 2);
+}
+
+template <int NW, int MODE, bool SHIST>
+constexpr size_t smem_bytes()
+{
+    return sizeof(WarpWork<NW>) * warps_per_block<NW>() +
+           (SHIST ? sizeof(unsigned long long) * (32 * NW + 2) * (32 * NW + 1) : 0);
+}
+
+template <int NW, int MODE, bool SHIST, bool PERSIST>
+__global__ void __launch_bounds__(32 * warps_per_block<NW>())
+    k_count(CountArgs A)
+{
+    constexpr int WPB = warps_per_block<NW>();
+    constexpr int D = 32 * NW;
+    extern __shared__ __align__(16) unsigned char smem[];
+    WarpWork<NW> *ww = reinterpret_cast<WarpWork<NW> *>(smem);
+    unsigned long long *shist = reinterpret_cast<unsigned long long *>(ww + WPB);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    WalkCounters wc;
+    if (SHIST) {
+        for (int i = threadIdx.x; i < (D + 2) * (D + 1); i += blockDim.x) shist[i] = 0;
+        __syncthreads();
+    }
+    for (;;) {
+        unsigned qi;
+        if (PERSIST) {
+            if (lane == 0) qi = atomicAdd(A.qhead, 1u);
+            qi = __shfl_sync(FULL, qi, 0);
+        } else {
+            qi = blockIdx.x * WPB + wid;
+        }
+        if (qi >= A.nroots) break;
+        walk_root<NW, MODE, SHIST>(ww[wid], shist, A, lane, A.roots[qi], wc);
+        if (!PERSIST) break;
+        if (*(volatile unsigned *)A.err & (DERR_STACK | DERR_RANGE)) break;
+    }
+    if (lane == 0 && wc.nodes) {
+        atomicAdd(&A.stats[0], wc.nodes);
+        atomicAdd(&A.stats[1], wc.leaves);
+        atomicAdd(&A.stats[2], wc.words);
+        atomicAdd(&A.stats[3 + A.cls], wc.words);
+    }
+    if (SHIST) {
+        __syncthreads();
+        for (int i = threadIdx.x; i < (D + 2) * (D + 1); i += blockDim.x) {
+            unsigned long long v = shist[i];
+            if (v) atomicAdd(&A.hist[(size_t)(i / (D + 1)) * A.hstride + (i % (D + 1))], v);
+        }
+    }
+}
+
+// ------------------------------------------------------ small kernels
+
+// Roots with no out-neighbour: one path each with h = 1, p = 0.
+__global__ void k_add_leaf(unsigned long long *cell, unsigned long long count)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) *cell += count;
+}
+
+// Local counts of roots with no out-neighbour: c_1(r) += 1.
+__global__ void k_vertex_trivial(const uint32_t *__restrict__ roots, unsigned nroots,
+                                 unsigned long long *cv, int K, int W)
+{
+    for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < nroots; i += gridDim.x * blockDim.x)
+        cv[((size_t)roots[i] * K + 1) * W] += 1ull;
+}
+
+// Multi-word Pascal table C(a, b), 0 <= b <= a < rows, by Pascal's rule,
+// one row at a time in a single block.
+__global__ void k_binom(unsigned long long *B, int rows, int W, unsigned *err)
+{
+    for (int a = 0; a < rows; ++a) {
+        for (int b = threadIdx.x; b <= a; b += blockDim.x) {
+            unsigned long long *dst = B + ((size_t)a * (a + 1) / 2 + b) * W;
+            if (b == 0 || b == a) {
+                dst[0] = 1;
+                for (int w = 1; w < W; ++w) dst[w] = 0;
+            } else {
+                const unsigned long long *x = B + ((size_t)(a - 1) * a / 2 + b - 1) * W;
+                const unsigned long long *y = x + W;
+                unsigned long long c = 0;
+                for (int w = 0; w < W; ++w) {
+                    unsigned long long s1 = x[w] + y[w];
+                    unsigned long long c1 = s1 < x[w];
+                    unsigned long long s2 = s1 + c;
+                    c = c1 + (s2 < s1);
+                    dst[w] = s2;
+                }
+                if (c) atomicOr(err, DERR_OVERFLOW);
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// C_k = sum over (h, p) of hist[h][p] * C(p, k - h), one block per k, exact.
+__global__ void __launch_bounds__(256) k_combine(const unsigned long long *__restrict__ hist,
+                                                 int hstride, const unsigned long long *__restrict__ B,
+                                                 int W, int kmax, unsigned long long *C, unsigned *err)
+{
+    __shared__ unsigned long long red[256][WMAX];
+    const int k = blockIdx.x;
+    unsigned long long acc[WMAX];
+#pragma unroll
+    for (int w = 0; w < WMAX; ++w) acc[w] = 0;
+    bool ovf = false;
+    const int pmax = hstride - 2;
+    const int hmax = min(k, hstride - 1);
+    const int total = hmax * (pmax + 1);  // pairs (h, p), h = 1..hmax
+    for (int t = threadIdx.x; t < total; t += blockDim.x) {
+        const int h = 1 + t / (pmax + 1), p = t % (pmax + 1);
+        const int i = k - h;
+        if (i < 0 || i > p) continue;
+        const unsigned long long x = hist[(size_t)h * hstride + p];
+        if (!x) continue;
+        const unsigned long long *b = B + ((size_t)p * (p + 1) / 2 + i) * W;
+        unsigned long long carry = 0;
+#pragma unroll
+        for (int w = 0; w < WMAX; ++w) {
+            if (w >= W) break;
+            unsigned long long lo = x * b[w], hi = __umul64hi(x, b[w]);
+            unsigned long long s1 = acc[w] + lo;
+            unsigned long long c1 = s1 < lo;
+            unsigned long long s2 = s1 + carry;
+            unsigned long long c2 = s2 < s1;
+            acc[w] = s2;
+            carry = hi + c1 + c2;
+        }
+        if (carry) ovf = true;
+    }
+#pragma unroll
+    for (int w = 0; w < WMAX; ++w) red[threadIdx.x][w] = acc[w];
+    __syncthreads();
+    for (int stride = 128; stride > 0; stride >>= 1) {
+        if (threadIdx.x < stride) {
+            unsigned long long c = 0;
+            for (int w = 0; w < W; ++w) {
+                unsigned long long x = red[threadIdx.x][w], y = red[threadIdx.x + stride][w];
+                unsigned long long s1 = x + y, c1 = s1 < x, s2 = s1 + c;
+                c = c1 + (s2 < s1);
+                red[threadIdx.x][w] = s2;
+            }
+            if (c) ovf = true;
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x < W) C[(size_t)k * W + threadIdx.x] = red[0][threadIdx.x];
+    if (ovf) atomicOr(err, DERR_OVERFLOW);
+}
+
+// ------------------------------------------------------------- driver
+
+template <typename T>
+static pvt_status grow(DevBuf<T> &b, size_t n, cudaStream_t s)
+{
+    if (b.n >= n) return PVT_OK;
+    if (b.p) PVT_CK(cudaFreeAsync(b.p, s));
+    b.p = nullptr;
+    b.n = 0;
+    PVT_CK(cudaMallocAsync(&b.p, n * sizeof(T), s));
+    b.n = n;
+    return PVT_OK;
+}
+
+static pvt_status ensure_binom(pvt_dag *g, int W, cudaStream_t s)
+{
+    const int rows = g->alpha + 3;
+    if (g->binom_rows == rows && g->binom_W == W) return PVT_OK;
+    pvt_status st = grow(g->binom, (size_t)rows * (rows + 1) / 2 * W, s);
+    if (st != PVT_OK) return st;
+    k_binom<<<1, 1024, 0, s>>>(g->binom.p, rows, W, g->d_err);
+    PVT_CK(cudaGetLastError());
+    g->stats.launches++;
+    g->binom_rows = rows;
+    g->binom_W = W;
+    return PVT_OK;
+}
+
+template <int NW, int MODE, bool SHIST>
+static pvt_status launch_class(pvt_dag *g, const CountArgs &base, int cls, cudaStream_t s)
+{
+    const unsigned cnt = (unsigned)g->class_cnt[cls];
+    if (cnt == 0) return PVT_OK;
+    CountArgs A = base;
+    A.roots = g->roots + g->class_start[cls];
+    A.nroots = cnt;
+    A.qhead = g->d_q + cls;
+    A.cls = cls;
+    constexpr size_t smem = smem_bytes<NW, MODE, SHIST>();
+    auto kern = k_count<NW, MODE, SHIST, true>;
+    PVT_CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    PVT_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * warps_per_block<NW>(), smem));
+    if (per_sm < 1) {
+        set_error("count kernel cannot be resident (shared memory)");
+        return PVT_ECUDA;
+    }
+    const unsigned need = (cnt + warps_per_block<NW>() - 1) / warps_per_block<NW>();
+    const unsigned grid = std::min<unsigned>((unsigned)(g->num_sms * per_sm), need);
+    phase_begin(g, 1 + cls, s);
+    kern<<<grid, 32 * warps_per_block<NW>(), smem, s>>>(A);
+    PVT_CK(cudaGetLastError());
+    phase_end(g, 1 + cls, s);
+    g->stats.launches++;
+    return PVT_OK;
+}
+
+template <int MODE>
+static pvt_status launch_all(pvt_dag *g, const CountArgs &A, cudaStream_t s)
+{
+    // heavy classes on side streams so that they overlap the light ones
+    PVT_CK(cudaEventRecord(g->ev_fork, s));
+    pvt_status st = PVT_OK;
+    for (int c = NCLASS - 1; c >= 1 && st == PVT_OK; --c) {
+        cudaStream_t cs = g->side[c];
+        PVT_CK(cudaStreamWaitEvent(cs, g->ev_fork, 0));
+        switch (c) {
+            case 1: st = launch_class<1, MODE, MODE == MODE_GLOBAL>(g, A, c, cs); break;
+            case 2: st = launch_class<2, MODE, MODE == MODE_GLOBAL>(g, A, c, cs); break;
+            case 3: st = launch_class<4, MODE, false>(g, A, c, cs); break;
+            case 4: st = launch_class<8, MODE, false>(g, A, c, cs); break;
+            case 5: st = launch_class<16, MODE, false>(g, A, c, cs); break;
+        }
+        PVT_CK(cudaEventRecord(g->ev_join[c], cs));
+    }
+    for (int c = NCLASS - 1; c >= 1; --c) PVT_CK(cudaStreamWaitEvent(s, g->ev_join[c], 0));
+    return st;
+}
+
+static void begin_call(pvt_dag *g)
+{
+    stats_reset(g);
+    for (int c = 0; c < NCLASS; ++c) g->stats.roots[c] = (uint64_t)g->class_cnt[c];
+}
+
+// Copy the walk statistics back, synchronise and check the device status.
+static pvt_status end_call(pvt_dag *g, cudaStream_t s, const char *fn)
+{
+    PVT_CK(cudaMemcpyAsync(g->h_stats, g->d_stats, (3 + NCLASS) * sizeof(unsigned long long),
+                           cudaMemcpyDeviceToHost, s));
+    pvt_status st = check_device(g, s, fn);
+    g->stats.sct_nodes = g->h_stats[0];
+    g->stats.sct_leaves = g->h_stats[1];
+    g->stats.pivot_words = g->h_stats[2];
+    for (int c = 0; c < NCLASS; ++c) g->stats.class_words[c] = g->h_stats[3 + c];
+    return st;
+}
+
+static pvt_status check_args(pvt_dag *g, int32_t kmax, int32_t W, const void *out, const char *fn)
+{
+    if (!g || !out || kmax < 0 || W < 1) {
+        set_error(std::string(fn) + ": invalid argument");
+        return PVT_EINVAL;
+    }
+    if (W < min_words(g->n, g->alpha)) {
+        set_error(std::string(fn) + ": W=" + std::to_string(W) + " below the required " +
+                  std::to_string(min_words(g->n, g->alpha)) + " words");
+        return PVT_EOVERFLOW;
+    }
+    if (W > WMAX) {
+        set_error(std::string(fn) + ": W above " + std::to_string(WMAX));
+        return PVT_EINVAL;
+    }
+    return PVT_OK;
+}
+
+pvt_status count_global(pvt_dag *g, int32_t kmax, int32_t W, uint64_t *C, cudaStream_t s)
+{
+    pvt_status st = check_args(g, kmax, W, C, "pvt_count_global");
+    if (st != PVT_OK) return st;
+    begin_call(g);
+    const int hstride = g->alpha + 2;
+    if ((st = grow(g->hist, (size_t)hstride * hstride, s)) != PVT_OK) return st;
+    if ((st = ensure_binom(g, W, s)) != PVT_OK) return st;
+    PVT_CK(cudaMemsetAsync(g->d_err, 0, sizeof(unsigned), s));
+    PVT_CK(cudaMemsetAsync(g->d_q, 0, 16 * sizeof(unsigned), s));
+    PVT_CK(cudaMemsetAsync(g->hist.p, 0, (size_t)hstride * hstride * sizeof(unsigned long long), s));
+    PVT_CK(cudaMemsetAsync(g->d_stats, 0, 16 * sizeof(unsigned long long), s));
+    if (g->class_cnt[0] && kmax >= 1) {
+        k_add_leaf<<<1, 32, 0, s>>>(g->hist.p + hstride, (unsigned long long)g->class_cnt[0]);
+        g->stats.launches++;
+    }
+    CountArgs A{};
+    A.orow = g->orow;
+    A.ocol = g->ocol;
+    A.hist = g->hist.p;
+    A.hstride = hstride;
+    A.B = g->binom.p;
+    A.W = W;
+    A.kmax = kmax;
+    A.err = g->d_err;
+    A.stats = g->d_stats;
+    if ((st = launch_all<MODE_GLOBAL>(g, A, s)) != PVT_OK) return st;
+    phase_begin(g, 7, s);
+    k_combine<<<kmax + 1, 256, 0, s>>>(g->hist.p, hstride, g->binom.p, W, kmax,
+                                       reinterpret_cast<unsigned long long *>(C), g->d_err);
+    PVT_CK(cudaGetLastError());
+    phase_end(g, 7, s);
+    g->stats.launches++;
+    return end_call(g, s, "pvt_count_global");
+}
+
+pvt_status count_local(pvt_dag *g, int32_t kmax, int32_t W, uint64_t *out, bool edge, cudaStream_t s)
+{
+    const char *fn = edge ? "pvt_count_local_edge" : "pvt_count_local_vertex";
+    pvt_status st = check_args(g, kmax, W, out, fn);
+    if (st != PVT_OK) return st;
+    begin_call(g);
+    if (edge && !g->oeid) {
+        if ((st = ensure_edge_ids(g, s)) != PVT_OK) return st;
+        g->stats.launches += 5;
+    }
+    if ((st = ensure_binom(g, W, s)) != PVT_OK) return st;
+    const int64_t rows = edge ? g->m : g->n;
+    PVT_CK(cudaMemsetAsync(g->d_err, 0, sizeof(unsigned), s));
+    PVT_CK(cudaMemsetAsync(g->d_q, 0, 16 * sizeof(unsigned), s));
+    PVT_CK(cudaMemsetAsync(out, 0, (size_t)rows * (kmax + 1) * W * sizeof(uint64_t), s));
+    PVT_CK(cudaMemsetAsync(g->d_stats, 0, 16 * sizeof(unsigned long long), s));
+    unsigned long long *o = reinterpret_cast<unsigned long long *>(out);
+    if (!edge && g->class_cnt[0] && kmax >= 1) {
+        k_vertex_trivial<<<g->num_sms * 4, 256, 0, s>>>(g->roots + g->class_start[0],
+                                                       (unsigned)g->class_cnt[0], o, kmax + 1, W);
+        g->stats.launches++;
+    }
+    CountArgs A{};
+    A.orow = g->orow;
+    A.ocol = g->ocol;
+    A.oeid = g->oeid;
+    A.out = o;
+    A.B = g->binom.p;
+    A.W = W;
+    A.kmax = kmax;
+    A.err = g->d_err;
+    A.stats = g->d_stats;
+    st = edge ? launch_all<MODE_EDGE>(g, A, s) : launch_all<MODE_VERTEX>(g, A, s);
+    if (st != PVT_OK) return st;
+    return end_call(g, s, fn);
+}
+
+}  // namespace pvt

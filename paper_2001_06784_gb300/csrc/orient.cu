@@ -1,0 +1,528 @@
+// Degeneracy orientation on the device (Lemma degen, Sec. 3.2; Alg. 1 step 1).
+//
+// 1. Optional CSR validation (simple undirected graph, Sec. 3.1).
+// 2. Level-synchronous k-core peeling in one cooperative kernel: at level k,
+//    every remaining vertex whose residual degree is <= k is removed in the
+//    current round; removals lower their neighbours' residual degrees, and
+//    neighbours that reach k join the next round.  When a level empties, k
+//    rises to the smallest remaining residual degree.  A vertex removed in
+//    round t had at most k <= alpha neighbours not removed before round t.
+// 3. The orientation u -> v iff (round[u], u) < (round[v], v): every
+//    out-neighbour of v was still present when v was removed, so every
+//    out-degree is at most the degeneracy.  Out-lists keep the CSR's
+//    ascending-id order.
+// 4. Roots grouped by out-degree class (bitset width), largest first.
+#include <cooperative_groups.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "pvt_internal.cuh"
+
+namespace pvt {
+
+// ------------------------------------------------------------ validation
+
+__global__ void k_validate(int64_t n, int64_t nnz, const int64_t *__restrict__ rp,
+                           const uint32_t *__restrict__ col, unsigned *err)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t v = warp; v < n; v += nwarps) {
+        int64_t b = rp[v], e = rp[v + 1];
+        if (b < 0 || e < b || e > nnz) {
+            if (lane == 0) atomicOr(err, DERR_NOTSIMPLE);
+            continue;
+        }
+        for (int64_t j = b + lane; j < e; j += 32) {
+            uint32_t u = col[j];
+            bool bad = (u >= (uint64_t)n) || (u == (uint64_t)v) || (j + 1 < e && col[j + 1] <= u);
+            if (!bad) {
+                // symmetry: v must be in row u
+                int64_t lo = rp[u], hi = rp[u + 1];
+                if (lo < 0 || hi < lo || hi > nnz) {
+                    bad = true;
+                } else {
+                    while (lo < hi) {
+                        int64_t mid = lo + ((hi - lo) >> 1);
+                        if (col[mid] < (uint32_t)v) lo = mid + 1; else hi = mid;
+                    }
+                    bad = !(lo < rp[u + 1] && col[lo] == (uint32_t)v);
+                }
+            }
+            if (bad) atomicOr(err, DERR_NOTSIMPLE);
+        }
+    }
+}
+
+// --------------------------------------------------------------- peeling
+
+struct PeelState {
+    unsigned cnt[3];      // rotating frontier sizes
+    unsigned min_deg;     // smallest residual degree among remaining vertices
+    unsigned bar_count;   // grid barrier arrivals
+    unsigned bar_gen;     // grid barrier generation
+    unsigned rounds;      // rounds used (diagnostic)
+    unsigned levels;      // levels visited (diagnostic)
+};
+
+constexpr unsigned long long BARRIER_LIMIT_NS = 4000000000ull;  // 4 s
+
+// Grid-wide barrier for a cooperative launch, with a bounded wait: on
+// timeout it sets DERR_TIMEOUT and every block leaves the kernel.
+__device__ bool grid_barrier(PeelState *st, unsigned *err)
+{
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned *vgen = &st->bar_gen;
+        unsigned gen = *vgen;
+        int ok = 1;
+        __threadfence();
+        unsigned arrived = atomicAdd(&st->bar_count, 1u) + 1u;
+        if (arrived == gridDim.x) {
+            st->bar_count = 0;
+            __threadfence();
+            atomicAdd(&st->bar_gen, 1u);
+        } else {
+            unsigned long long t0 = global_ns();
+            while (*vgen == gen) {
+                if (*(volatile unsigned *)err & DERR_TIMEOUT) { ok = 0; break; }
+                if (global_ns() - t0 > BARRIER_LIMIT_NS) {
+                    atomicOr(err, DERR_TIMEOUT);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+__global__ void __launch_bounds__(512) k_peel(int64_t n, const int64_t *__restrict__ rp,
+                                              const uint32_t *__restrict__ col, uint32_t *deg,
+                                              uint32_t *rnd, uint32_t *core, uint32_t *fa,
+                                              uint32_t *fb, PeelState *st, unsigned *err)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
+    const int64_t warp = tid >> 5, nwarps = nthreads >> 5;
+    volatile PeelState *vst = st;
+
+    for (int64_t v = tid; v < n; v += nthreads) {
+        deg[v] = (uint32_t)(rp[v + 1] - rp[v]);
+        rnd[v] = NOT_REMOVED;
+    }
+    if (!grid_barrier(st, err)) return;
+
+    unsigned k = 0, round = 0;
+    uint32_t *cur = fa, *nxt = fb;
+    for (;;) {
+        // ---- level start: smallest residual degree among remaining vertices
+        if (tid == 0) { st->min_deg = NOT_REMOVED; st->cnt[round % 3] = 0; }
+        if (!grid_barrier(st, err)) return;
+        {
+            unsigned mine = NOT_REMOVED;
+            for (int64_t v = tid; v < n; v += nthreads)
+                if (rnd[v] == NOT_REMOVED) mine = min(mine, deg[v]);
+            for (int o = 16; o; o >>= 1) mine = min(mine, __shfl_xor_sync(FULL, mine, o));
+            if (lane == 0 && mine != NOT_REMOVED) atomicMin(&st->min_deg, mine);
+        }
+        if (!grid_barrier(st, err)) return;
+        unsigned md = vst->min_deg;
+        if (md == NOT_REMOVED) break;  // every vertex removed
+        k = max(k, md);
+        if (tid == 0) st->levels++;
+        // ---- this level's first frontier: all remaining with deg <= k
+        for (int64_t v = tid; v < n; v += nthreads) {
+            if (rnd[v] == NOT_REMOVED && deg[v] <= k) {
+                rnd[v] = round;
+                core[v] = k;
+                cur[atomicAdd(&st->cnt[round % 3], 1u)] = (uint32_t)v;
+            }
+        }
+        if (!grid_barrier(st, err)) return;
+        // ---- rounds of this level
+        for (;;) {
+            unsigned fsize = vst->cnt[round % 3];
+            if (fsize == 0) break;
+            if (tid == 0) st->cnt[(round + 2) % 3] = 0;  // free since last round
+            // relax: neighbours reaching k join round+1 (marked on entry)
+            for (int64_t i = warp; i < fsize; i += nwarps) {
+                uint32_t v = cur[i];
+                for (int64_t j = rp[v] + lane; j < rp[v + 1]; j += 32) {
+                    uint32_t u = col[j];
+                    if (rnd[u] == NOT_REMOVED) {
+                        unsigned old = atomicSub(&deg[u], 1u);
+                        if (old == k + 1) {
+                            rnd[u] = round + 1;
+                            core[u] = k;
+                            nxt[atomicAdd(&st->cnt[(round + 1) % 3], 1u)] = u;
+                        }
+                    }
+                }
+            }
+            if (!grid_barrier(st, err)) return;
+            ++round;
+            uint32_t *t = cur; cur = nxt; nxt = t;
+        }
+        // the empty frontier counter cnt[round % 3] is reset at the next level start
+    }
+    if (tid == 0) st->rounds = round;
+}
+
+// ------------------------------------------------------------ orientation
+
+__device__ __forceinline__ bool key_less(uint32_t ra, uint32_t a, uint32_t rb, uint32_t b)
+{
+    return ra < rb || (ra == rb && a < b);
+}
+
+// Out-degree of every vertex (warp per vertex) and the largest one.
+__global__ void k_outdeg(int64_t n, const int64_t *__restrict__ rp, const uint32_t *__restrict__ col,
+                         const uint32_t *__restrict__ rnd, uint32_t *odeg, unsigned *alpha)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t v = warp; v < n; v += nwarps) {
+        uint32_t rv = rnd[v];
+        unsigned c = 0;
+        for (int64_t j = rp[v] + lane; j < rp[v + 1]; j += 32) {
+            uint32_t u = col[j];
+            c += key_less(rv, (uint32_t)v, rnd[u], u);
+        }
+        for (int o = 16; o; o >>= 1) c += __shfl_xor_sync(FULL, c, o);
+        if (lane == 0) {
+            odeg[v] = c;
+            atomicMax(alpha, c);
+        }
+    }
+}
+
+// Out-lists in CSR order (ascending id), compacted with a warp ballot.
+__global__ void k_fill(int64_t n, const int64_t *__restrict__ rp, const uint32_t *__restrict__ col,
+                       const uint32_t *__restrict__ rnd, const int64_t *__restrict__ orow,
+                       uint32_t *ocol)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t v = warp; v < n; v += nwarps) {
+        uint32_t rv = rnd[v];
+        int64_t out = orow[v];
+        for (int64_t j0 = rp[v]; j0 < rp[v + 1]; j0 += 32) {
+            int64_t j = j0 + lane;
+            uint32_t u = 0;
+            bool keep = false;
+            if (j < rp[v + 1]) {
+                u = col[j];
+                keep = key_less(rv, (uint32_t)v, rnd[u], u);
+            }
+            unsigned b = __ballot_sync(FULL, keep);
+            if (keep) ocol[out + __popc(b & ((1u << lane) - 1u))] = u;
+            out += __popc(b);
+        }
+    }
+}
+
+// Class of an out-degree: 0 for d = 0, else 1 + ceil(log2(ceil(d / 32))).
+__host__ __device__ inline int degree_class(uint32_t d)
+{
+    if (d == 0) return 0;
+    int c = 1;
+    uint32_t cap = 32;
+    while (d > cap) { cap <<= 1; ++c; }
+    return c;
+}
+
+__global__ void k_deg_hist(int64_t n, const uint32_t *__restrict__ odeg, unsigned *hist)
+{
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
+         v += (int64_t)gridDim.x * blockDim.x)
+        atomicAdd(&hist[odeg[v]], 1u);
+}
+
+// Scatter roots so that out-degrees descend within the array (slot[d] holds
+// the next free position for out-degree d).
+__global__ void k_deg_scatter(int64_t n, const uint32_t *__restrict__ odeg, unsigned *slot,
+                              uint32_t *roots)
+{
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
+         v += (int64_t)gridDim.x * blockDim.x)
+        roots[atomicAdd(&slot[odeg[v]], 1u)] = (uint32_t)v;
+}
+
+// ------------------------------------------------------------------ scan
+
+__global__ void k_scan_blocks(const uint32_t *__restrict__ in, int64_t *out, int64_t n,
+                              unsigned long long *bsum)
+{
+    // exclusive scan of one 1024-element tile per block; tile total to bsum
+    __shared__ unsigned long long ws[32];
+    int64_t i = blockIdx.x * 1024ll + threadIdx.x;
+    unsigned long long x = i < n ? in[i] : 0;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    unsigned long long inc = x;
+    for (int o = 1; o < 32; o <<= 1) {
+        unsigned long long t = __shfl_up_sync(FULL, inc, o);
+        if (lane >= o) inc += t;
+    }
+    if (lane == 31) ws[wid] = inc;
+    __syncthreads();
+    if (wid == 0) {
+        unsigned long long w = ws[lane], wi = w;
+        for (int o = 1; o < 32; o <<= 1) {
+            unsigned long long t = __shfl_up_sync(FULL, wi, o);
+            if (lane >= o) wi += t;
+        }
+        ws[lane] = wi - w;
+        if (lane == 31) bsum[blockIdx.x] = wi;
+    }
+    __syncthreads();
+    if (i < n) out[i] = (int64_t)(inc - x + ws[wid]);
+}
+
+__global__ void k_scan_sums(unsigned long long *bsum, int64_t nb, int64_t *total_out)
+{
+    // single block: exclusive scan of the tile totals in place
+    __shared__ unsigned long long carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    __shared__ unsigned long long ws[32];
+    for (int64_t base = 0; base < nb; base += 1024) {
+        int64_t i = base + threadIdx.x;
+        unsigned long long x = i < nb ? bsum[i] : 0, inc = x;
+        for (int o = 1; o < 32; o <<= 1) {
+            unsigned long long t = __shfl_up_sync(FULL, inc, o);
+            if (lane >= o) inc += t;
+        }
+        if (lane == 31) ws[wid] = inc;
+        __syncthreads();
+        if (wid == 0) {
+            unsigned long long w = ws[lane], wi = w;
+            for (int o = 1; o < 32; o <<= 1) {
+                unsigned long long t = __shfl_up_sync(FULL, wi, o);
+                if (lane >= o) wi += t;
+            }
+            ws[lane] = wi - w;
+        }
+        __syncthreads();
+        unsigned long long c = carry;
+        if (i < nb) bsum[i] = c + inc - x + ws[wid];
+        __syncthreads();
+        if (threadIdx.x == 1023) carry = c + inc + ws[wid];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *total_out = (int64_t)carry;
+}
+
+__global__ void k_scan_add(int64_t *out, int64_t n, const unsigned long long *__restrict__ bsum)
+{
+    int64_t i = blockIdx.x * 1024ll + threadIdx.x;
+    if (i < n) out[i] += (int64_t)bsum[blockIdx.x];
+}
+
+pvt_status exclusive_scan_u32_i64(const uint32_t *in, int64_t *out, int64_t n, cudaStream_t s)
+{
+    int64_t nb = (n + 1023) / 1024;
+    unsigned long long *bsum = nullptr;
+    PVT_CK(cudaMallocAsync(&bsum, (size_t)std::max<int64_t>(nb, 1) * sizeof(unsigned long long), s));
+    if (nb > 0) k_scan_blocks<<<(unsigned)nb, 1024, 0, s>>>(in, out, n, bsum);
+    k_scan_sums<<<1, 1024, 0, s>>>(bsum, nb, out + n);
+    if (nb > 0) k_scan_add<<<(unsigned)nb, 1024, 0, s>>>(out, n, bsum);
+    PVT_CK(cudaGetLastError());
+    PVT_CK(cudaFreeAsync(bsum, s));
+    return PVT_OK;
+}
+
+// ------------------------------------------------------------- edge ids
+
+// Edge id of every out-edge r -> u: rank of (min, max) in lexicographic
+// order = up[a] + (position of b in row a) - (position of the first entry
+// > a in row a), with a = min, b = max and up[a] = edges (x, y), x < y, x < a.
+__global__ void k_upper_count(int64_t n, const int64_t *__restrict__ rp,
+                              const uint32_t *__restrict__ col, uint32_t *cnt)
+{
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
+         v += (int64_t)gridDim.x * blockDim.x) {
+        int64_t lo = rp[v], hi = rp[v + 1], e = hi;
+        while (lo < hi) {
+            int64_t mid = lo + ((hi - lo) >> 1);
+            if (col[mid] <= (uint32_t)v) lo = mid + 1; else hi = mid;
+        }
+        cnt[v] = (uint32_t)(e - lo);
+    }
+}
+
+__device__ __forceinline__ int64_t lower_bound_row(const uint32_t *__restrict__ col, int64_t lo,
+                                                   int64_t hi, uint32_t x)
+{
+    while (lo < hi) {
+        int64_t mid = lo + ((hi - lo) >> 1);
+        if (col[mid] < x) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+__global__ void k_edge_ids(int64_t n, const int64_t *__restrict__ rp, const uint32_t *__restrict__ col,
+                           const int64_t *__restrict__ up, const int64_t *__restrict__ orow,
+                           const uint32_t *__restrict__ ocol, uint32_t *oeid)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t r = warp; r < n; r += nwarps) {
+        for (int64_t j = orow[r] + lane; j < orow[r + 1]; j += 32) {
+            uint32_t u = ocol[j];
+            uint32_t a = min((uint32_t)r, u), b = max((uint32_t)r, u);
+            int64_t pos = lower_bound_row(col, rp[a], rp[a + 1], b);
+            int64_t first = lower_bound_row(col, rp[a], rp[a + 1], a + 1);
+            oeid[j] = (uint32_t)(up[a] + (pos - first));
+        }
+    }
+}
+
+pvt_status ensure_edge_ids(pvt_dag *g, cudaStream_t s)
+{
+    if (g->oeid || g->m == 0) return PVT_OK;
+    if (g->m > 0xFFFFFFFFll) {
+        set_error("pvt_count_local_edge: more than 2^32 edges");
+        return PVT_EINVAL;
+    }
+    uint32_t *cnt = nullptr;
+    int64_t *up = nullptr;
+    PVT_CK(cudaMallocAsync(&cnt, (size_t)g->n * sizeof(uint32_t) + 4, s));
+    PVT_CK(cudaMallocAsync(&up, (size_t)(g->n + 1) * sizeof(int64_t), s));
+    PVT_CK(cudaMallocAsync(&g->oeid, (size_t)g->m * sizeof(uint32_t), s));
+    int grid = g->num_sms * 8;
+    k_upper_count<<<grid, 256, 0, s>>>(g->n, g->row_ptr, g->col, cnt);
+    pvt_status st = exclusive_scan_u32_i64(cnt, up, g->n, s);
+    if (st != PVT_OK) return st;
+    k_edge_ids<<<grid, 256, 0, s>>>(g->n, g->row_ptr, g->col, up, g->orow, g->ocol, g->oeid);
+    PVT_CK(cudaGetLastError());
+    PVT_CK(cudaFreeAsync(cnt, s));
+    PVT_CK(cudaFreeAsync(up, s));
+    return PVT_OK;
+}
+
+// ---------------------------------------------------------------- driver
+
+pvt_status orient_build(pvt_dag *g, uint32_t flags, cudaStream_t s)
+{
+    const int64_t n = g->n;
+    const int grid = g->num_sms * 8;
+    PVT_CK(cudaMemsetAsync(g->d_err, 0, sizeof(unsigned), s));
+    if (flags & PVT_VALIDATE) {
+        k_validate<<<grid, 256, 0, s>>>(n, g->nnz, g->row_ptr, g->col, g->d_err);
+        PVT_CK(cudaGetLastError());
+        g->stats.launches++;
+        pvt_status st = check_device(g, s, "pvt_orient: CSR validation");
+        if (st != PVT_OK) return st;
+    }
+
+    uint32_t *deg = nullptr, *fa = nullptr, *fb = nullptr, *odeg = nullptr;
+    unsigned *dhist = nullptr;
+    PeelState *pst = nullptr;
+    const size_t nb = (size_t)std::max<int64_t>(n, 1) * sizeof(uint32_t);
+    PVT_CK(cudaMallocAsync(&deg, nb, s));
+    PVT_CK(cudaMallocAsync(&fa, nb, s));
+    PVT_CK(cudaMallocAsync(&fb, nb, s));
+    PVT_CK(cudaMallocAsync(&pst, sizeof(PeelState) + sizeof(unsigned), s));
+    PVT_CK(cudaMallocAsync(&g->rnd, nb, s));
+    PVT_CK(cudaMallocAsync(&g->core, nb, s));
+    PVT_CK(cudaMemsetAsync(pst, 0, sizeof(PeelState) + sizeof(unsigned), s));
+
+    // one cooperative launch: every block must be resident at once
+    int per_sm = 0;
+    PVT_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_peel, 512, 0));
+    per_sm = std::min(per_sm, 2);
+    if (per_sm < 1) {
+        set_error("pvt_orient: peel kernel cannot be resident");
+        return PVT_ECUDA;
+    }
+    {
+        int64_t nn = n;
+        const int64_t *rp = g->row_ptr;
+        const uint32_t *col = g->col;
+        uint32_t *rnd = g->rnd, *core = g->core;
+        unsigned *err = g->d_err;
+        void *args[] = {&nn, &rp, &col, &deg, &rnd, &core, &fa, &fb, &pst, &err};
+        phase_begin(g, 0, s);
+        PVT_CK(cudaLaunchCooperativeKernel((void *)k_peel, dim3(g->num_sms * per_sm), dim3(512), args,
+                                           0, s));
+        phase_end(g, 0, s);
+        g->stats.launches++;
+    }
+    phase_begin(g, 1, s);
+
+    // orientation
+    unsigned *d_alpha = (unsigned *)(pst + 1);
+    PVT_CK(cudaMallocAsync(&odeg, nb + sizeof(uint32_t), s));
+    PVT_CK(cudaMallocAsync(&g->orow, (size_t)(n + 1) * sizeof(int64_t), s));
+    k_outdeg<<<grid, 256, 0, s>>>(n, g->row_ptr, g->col, g->rnd, odeg, d_alpha);
+    PVT_CK(cudaGetLastError());
+    pvt_status st = exclusive_scan_u32_i64(odeg, g->orow, n, s);
+    g->stats.launches += 4;
+    if (st != PVT_OK) return st;
+    unsigned alpha = 0;
+    PVT_CK(cudaMemcpyAsync(&alpha, d_alpha, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+    PVT_CK(cudaStreamSynchronize(s));
+    st = check_device(g, s, "pvt_orient: peeling");
+    if (st != PVT_OK) return st;
+    g->alpha = (int32_t)alpha;
+    if (g->alpha > MAX_ALPHA) {
+        set_error("pvt_orient: degeneracy " + std::to_string(alpha) + " above the supported " +
+                  std::to_string(MAX_ALPHA));
+        return PVT_EINVAL;
+    }
+    PVT_CK(cudaMallocAsync(&g->ocol, (size_t)std::max<int64_t>(g->m, 1) * sizeof(uint32_t), s));
+    k_fill<<<grid, 256, 0, s>>>(n, g->row_ptr, g->col, g->rnd, g->orow, g->ocol);
+    PVT_CK(cudaGetLastError());
+    g->stats.launches++;
+
+    // roots by descending out-degree (counting sort), grouped into classes
+    const int nd = g->alpha + 1;
+    PVT_CK(cudaMallocAsync(&dhist, (size_t)nd * sizeof(unsigned), s));
+    PVT_CK(cudaMemsetAsync(dhist, 0, (size_t)nd * sizeof(unsigned), s));
+    k_deg_hist<<<grid, 256, 0, s>>>(n, odeg, dhist);
+    g->stats.launches++;
+    std::vector<unsigned> hh(nd), slot(nd);
+    PVT_CK(cudaMemcpyAsync(hh.data(), dhist, (size_t)nd * sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+    PVT_CK(cudaStreamSynchronize(s));
+    // positions: larger out-degrees first; class c (degree range) is then a
+    // contiguous slice, higher classes first
+    unsigned pos = 0;
+    for (int d = nd - 1; d >= 0; --d) { slot[d] = pos; pos += hh[d]; }
+    for (int c = 0; c < NCLASS; ++c) g->class_cnt[c] = 0;
+    for (int d = 0; d < nd; ++d) g->class_cnt[degree_class((uint32_t)d)] += hh[d];
+    {
+        int64_t off = 0;
+        for (int c = NCLASS - 1; c >= 0; --c) { g->class_start[c] = off; off += g->class_cnt[c]; }
+    }
+    PVT_CK(cudaMemcpyAsync(dhist, slot.data(), (size_t)nd * sizeof(unsigned), cudaMemcpyHostToDevice, s));
+    PVT_CK(cudaMallocAsync(&g->roots, nb, s));
+    k_deg_scatter<<<grid, 256, 0, s>>>(n, odeg, dhist, g->roots);
+    PVT_CK(cudaGetLastError());
+    phase_end(g, 1, s);
+    g->stats.launches++;
+    for (int c = 0; c < NCLASS; ++c) g->stats.roots[c] = (uint64_t)g->class_cnt[c];
+
+    PVT_CK(cudaFreeAsync(deg, s));
+    PVT_CK(cudaFreeAsync(fa, s));
+    PVT_CK(cudaFreeAsync(fb, s));
+    PVT_CK(cudaFreeAsync(pst, s));
+    PVT_CK(cudaFreeAsync(odeg, s));
+    PVT_CK(cudaFreeAsync(dhist, s));
+    PVT_CK(cudaStreamSynchronize(s));
+    return check_device(g, s, "pvt_orient");
+}
+
+}  // namespace pvt

@@ -1,0 +1,119 @@
+// Internal definitions shared by the CUDA translation units of libpivoter.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "pivoter.h"
+
+namespace pvt {
+
+constexpr unsigned FULL = 0xFFFFFFFFu;
+constexpr uint32_t NOT_REMOVED = 0xFFFFFFFFu;
+
+// Root classes by out-degree d = |N+(r)|: class 0 holds d = 0, class c >= 1
+// holds 32 * 2^(c-2) < d <= 32 * 2^(c-1), i.e. bitsets of NW = 2^(c-1) words.
+constexpr int NCLASS = 6;              // d = 0, <=32, <=64, <=128, <=256, <=512
+constexpr int MAX_ALPHA = 512;         // largest out-degree with shared-memory bitsets
+constexpr int WMAX = 20;               // largest W (64-bit words per count) supported
+
+// Device-side error bits (one 32-bit status word per dag).
+enum : unsigned {
+    DERR_STACK = 1u,      // explicit DFS stack would overflow (capacity bug)
+    DERR_TIMEOUT = 2u,    // bounded spin-wait gave up
+    DERR_OVERFLOW = 4u,   // multi-word arithmetic carried out of the top word
+    DERR_RANGE = 8u,      // an index fell outside its table (capacity bug)
+    DERR_NOTSIMPLE = 16u  // CSR validation failed
+};
+
+// Per-call scratch that lives as long as the dag (grown on demand).
+template <typename T>
+struct DevBuf {
+    T *p = nullptr;
+    size_t n = 0;
+};
+
+}  // namespace pvt
+
+struct pvt_dag {
+    int device = 0;
+    int num_sms = 0;
+    int64_t n = 0, m = 0, nnz = 0;
+    int32_t alpha = 0;
+    const int64_t *row_ptr = nullptr;  // borrowed undirected CSR
+    const uint32_t *col = nullptr;
+    // owned device state
+    uint32_t *rnd = nullptr;       // peel round of each vertex (orientation key high part)
+    uint32_t *core = nullptr;      // peel level (core number) of each vertex
+    int64_t *orow = nullptr;       // DAG CSR row pointers, int64[n+1]
+    uint32_t *ocol = nullptr;      // DAG out-neighbours, sorted by id, uint32[m]
+    uint32_t *oeid = nullptr;      // edge id of each out-edge (built on first use)
+    uint32_t *roots = nullptr;     // roots grouped by class, descending out-degree
+    int64_t class_start[pvt::NCLASS] = {0};  // first position of each class in roots
+    int64_t class_cnt[pvt::NCLASS] = {0};
+    unsigned *d_err = nullptr;     // device status word
+    unsigned *d_q = nullptr;       // work-queue heads [16]
+    unsigned *h_err = nullptr;     // pinned host copy of the status word
+    pvt::DevBuf<unsigned long long> hist;   // (h, p) leaf histogram
+    pvt::DevBuf<unsigned long long> binom;  // multi-word Pascal table
+    int binom_rows = 0, binom_W = 0;
+    cudaStream_t side[pvt::NCLASS] = {};    // per-class streams for concurrent launches
+    cudaEvent_t ev_fork = nullptr, ev_join[pvt::NCLASS] = {};
+    // statistics and phase timing of the last call
+    unsigned long long *d_stats = nullptr;  // [0] nodes, [1] leaves, [2] pivot words
+    unsigned long long *h_stats = nullptr;  // pinned host copy
+    pvt_stats stats = {};
+    bool profiling = false;
+    cudaEvent_t ev_t0[8] = {}, ev_t1[8] = {};
+    bool phase_used[8] = {};
+};
+
+namespace pvt {
+
+// Thread-local error message used by pvt_last_error().
+void set_error(const std::string &msg);
+
+// Words needed so every count fits: each count is at most n * 2^alpha.
+int32_t min_words(int64_t n, int32_t alpha);
+
+// Map a CUDA error to a status (and record its message).
+pvt_status cuda_fail(cudaError_t e, const char *what);
+
+#define PVT_CK(call)                                          \
+    do {                                                      \
+        cudaError_t _e = (call);                              \
+        if (_e != cudaSuccess) return pvt::cuda_fail(_e, #call); \
+    } while (0)
+
+// Orientation (orient.cu).
+pvt_status orient_build(pvt_dag *g, uint32_t flags, cudaStream_t s);
+pvt_status ensure_edge_ids(pvt_dag *g, cudaStream_t s);
+
+// Counting (count.cu).
+pvt_status count_global(pvt_dag *g, int32_t kmax, int32_t W, uint64_t *C, cudaStream_t s);
+pvt_status count_local(pvt_dag *g, int32_t kmax, int32_t W, uint64_t *out, bool edge,
+                       cudaStream_t s);
+
+// Exclusive prefix sum of uint32 counts into int64 offsets (out has n+1 entries).
+pvt_status exclusive_scan_u32_i64(const uint32_t *in, int64_t *out, int64_t n, cudaStream_t s);
+
+// Phase timing: record the start / end event of phase `ph` on stream s (no-op
+// unless profiling is on).
+void phase_begin(pvt_dag *g, int ph, cudaStream_t s);
+void phase_end(pvt_dag *g, int ph, cudaStream_t s);
+void stats_reset(pvt_dag *g);
+
+// Read the device status word (synchronises s) and map it to a status.
+pvt_status check_device(pvt_dag *g, cudaStream_t s, const char *what);
+
+// Nanosecond clock for bounded waits.
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+}  // namespace pvt

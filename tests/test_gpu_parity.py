@@ -1,0 +1,224 @@
+"""GPU path vs the CPU oracle, word for word (integer results: tolerance 0).
+
+Every call goes through the C ABI (paper_2001_06784_gb300 binds it with
+ctypes).  Graphs span every bitset class of the root out-degree (<=32, <=64,
+<=128, <=256, <=512), ragged sizes, empty graphs and isolated vertices.
+"""
+from __future__ import annotations
+
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2001_06784_gb300 import graphgen
+from tests import graphs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pvt():
+    import torch  # noqa: F401
+
+    import paper_2001_06784_gb300 as p
+    return p
+
+
+def gpu_dag(pvt, rp, col, validate=True):
+    import torch
+    dev = torch.device("cuda:0")
+    col32 = np.ascontiguousarray(col, dtype=np.uint32).view(np.int32)
+    return pvt.orient(torch.from_numpy(np.ascontiguousarray(rp)).to(dev), torch.from_numpy(col32).to(dev),
+                      validate=validate)
+
+
+def check_all(pvt, rp, col, vertex=True, edge=True, kmax=None):
+    ref = oracle.count(rp, col, vertex=vertex, edge=edge, kmax=-1 if kmax is None else kmax)
+    dag = gpu_dag(pvt, rp, col)
+    K = ref["kmax"]
+    assert pvt.to_ints(dag.count_global(kmax=K)) == ref["C"]
+    if vertex:
+        assert pvt.to_ints(dag.count_local_vertex(kmax=K)) == oracle.to_int(ref["cv"])
+    if edge:
+        got = pvt.to_ints(dag.count_local_edge(kmax=K))
+        assert got == oracle.to_int(ref["ce"])
+    dag.free()
+    return ref
+
+
+def exact_column_sums(t):
+    """Exact sum over rows of a word table [rows, K, W] (uint64 words), as
+    K Python ints: 32-bit halves summed in uint64 cannot wrap below 2^32 rows."""
+    t = np.asarray(t, dtype=np.uint64)
+    lo = (t & np.uint64(0xFFFFFFFF)).sum(axis=0, dtype=np.uint64)
+    hi = (t >> np.uint64(32)).sum(axis=0, dtype=np.uint64)
+    out = []
+    for k in range(t.shape[1]):
+        out.append(sum((int(lo[k, w]) + (int(hi[k, w]) << 32)) << (64 * w) for w in range(t.shape[2])))
+    return out
+
+
+SMALL = {
+    "K1": lambda: graphs.complete(1),
+    "K2": lambda: graphs.complete(2),
+    "empty5": lambda: graphgen.from_edges(5, np.zeros((0, 2), dtype=np.int64)),
+    "K5": lambda: graphs.complete(5),
+    "K32": lambda: graphs.complete(33),          # alpha = 32: top of the 1-word class
+    "K34": lambda: graphs.complete(34),          # alpha = 33: 2-word class
+    "cliques": lambda: graphs.disjoint_cliques([3, 5, 7, 4, 1, 2, 12]),
+    "multipartite": lambda: graphs.multipartite([3, 3, 3, 3, 2, 1]),
+    "K50-star": lambda: graphs.clique_minus_star(50, 7, 9),
+    "gnp40": lambda: graphs.gnp(40, 0.35, 1),
+    "gnp70": lambda: graphs.gnp(70, 0.25, 2),
+    "gnp33": lambda: graphs.gnp(33, 0.6, 3),
+    "er-planted": lambda: graphgen.generate(500, er_avg_deg=8.0, planted=[(3, 10, 25, 1.0), (2, 30, 45, 0.9)],
+                                            seed=11),
+}
+
+
+@pytest.mark.parametrize("name", sorted(SMALL))
+def test_small_all_counts(pvt, name):
+    rp, col = SMALL[name]()
+    check_all(pvt, rp, col)
+
+
+@pytest.mark.parametrize("n", [70, 100, 130, 200, 257, 300])
+def test_wide_cliques_global_vertex(pvt, n):
+    # alpha = n-1 covers the 3-, 4-, 5-word... classes; counts are C(n, k)
+    rp, col = graphs.complete(n)
+    ref = check_all(pvt, rp, col, edge=False)
+    assert ref["C"][1:] == [math.comb(n, k) for k in range(1, n + 1)]
+
+
+@pytest.mark.parametrize("n,centre,k", [(100, 10, 20), (180, 3, 60), (260, 100, 40)])
+def test_wide_branching_global(pvt, n, centre, k):
+    rp, col = graphs.clique_minus_star(n, centre, k)
+    check_all(pvt, rp, col, vertex=True, edge=False)
+
+
+def test_wide_random_dense_global(pvt):
+    # dense random part with roots in the 65..128 class and real branching
+    rp, col = graphgen.generate(400, er_avg_deg=4.0, planted=[(1, 110, 110, 0.97), (3, 40, 70, 0.9)], seed=5)
+    check_all(pvt, rp, col, vertex=True, edge=False)
+
+
+@pytest.mark.parametrize("kmax", [0, 1, 2, 3, 5, 9])
+def test_truncation(pvt, kmax):
+    rp, col = graphgen.generate(400, er_avg_deg=10.0, planted=[(2, 15, 25, 1.0)], seed=3)
+    check_all(pvt, rp, col, kmax=kmax)
+
+
+def test_extra_words_are_zero(pvt):
+    rp, col = graphs.complete(40)
+    dag = gpu_dag(pvt, rp, col)
+    W = dag.min_words + 2
+    C = dag.count_global(W=W).cpu().numpy().view(np.uint64)
+    assert (C[:, dag.min_words:] == 0).all()
+    assert pvt.to_ints(C) == [0] + [math.comb(40, k) for k in range(1, 41)] + [0]
+
+
+def test_workload_er2k_all(pvt):
+    rp, col = graphgen.workload("er2k_d20_clique30")
+    check_all(pvt, rp, col)
+
+
+def test_repeat_calls_identical(pvt):
+    rp, col = graphgen.generate(3000, er_avg_deg=15.0, planted=[(5, 20, 40, 0.95)], seed=9)
+    dag = gpu_dag(pvt, rp, col)
+    a = pvt.to_ints(dag.count_global())
+    b = pvt.to_ints(dag.count_global())
+    v1 = dag.count_local_vertex().cpu().numpy()
+    v2 = dag.count_local_vertex().cpu().numpy()
+    assert a == b and (v1 == v2).all()
+
+
+# ------------------------------------------------------------ full sizes
+
+@pytest.mark.parametrize("name", ["cl1m_m10m_b2.1_comm500", "cl500k_m8m_b2.3_clq200"])
+def test_workload_full_global(pvt, name):
+    """Full-size global counts vs the root-parallel oracle on every host core."""
+    rp, col = graphgen.workload(name)
+    ref = oracle.count(rp, col, threads=os.cpu_count() or 1)
+    dag = gpu_dag(pvt, rp, col, validate=True)
+    assert dag.alpha <= ref["alpha"] + 0  # both are degeneracies of the same graph
+    got = pvt.to_ints(dag.count_global(kmax=ref["kmax"]))
+    assert got == ref["C"]
+    n, m = len(rp) - 1, len(col) // 2
+    assert got[1] == n and got[2] == m
+
+
+def test_workload_local_sampled(pvt):
+    """Per-vertex / per-edge tables at full size (500k vertices, 8M edges),
+    checked on sampled rows one by one: c_k(v) = C_{k-1} of the subgraph
+    induced on N(v), c_k(uv) = C_{k-2} of the subgraph on N(u) & N(v)
+    (definitions, Sec. 3.1), plus the identities sum_v c_k(v) = k C_k and
+    sum_e c_k(e) = C(k,2) C_k against the GPU's own global counts."""
+    rp, col = graphgen.workload("cl500k_m8m_b2.3_clq200")
+    n, m = len(rp) - 1, len(col) // 2
+    dag = gpu_dag(pvt, rp, col)
+    C = pvt.to_ints(dag.count_global())
+    K = max(k for k, c in enumerate(C) if c)  # clique number: every nonzero count
+    C = C[:K + 1]
+    cv = dag.count_local_vertex(kmax=K).cpu().numpy().view(np.uint64)
+    rng = np.random.default_rng(0)
+    deg = np.diff(rp)
+    sample = list(rng.choice(n, 40, replace=False)) + list(np.argsort(deg)[-5:])
+    for v in sample:
+        nb = col[rp[v]:rp[v + 1]].astype(np.int64)
+        srp, scol = graphgen.induced_subgraph(rp, col, nb)
+        sub = oracle.count(srp, scol, kmax=K - 1)["C"] if len(nb) else [0] * K
+        sub[0] = 1  # the empty clique extends to {v}
+        assert pvt.to_ints(cv[v]) == [0] + sub[:K], f"vertex {v}"
+    # identity: sum_v c_k(v) = k * C_k, in exact integers
+    assert exact_column_sums(cv) == [k * C[k] for k in range(K + 1)]
+    del cv
+    ce = dag.count_local_edge(kmax=K).cpu().numpy().view(np.uint64)
+    edges = graphgen.edge_list(rp, col)
+    for e in rng.choice(m, 30, replace=False):
+        u, v = edges[e]
+        common = np.intersect1d(col[rp[u]:rp[u + 1]], col[rp[v]:rp[v + 1]]).astype(np.int64)
+        if len(common):
+            srp, scol = graphgen.induced_subgraph(rp, col, common)
+            sub = oracle.count(srp, scol, kmax=max(K - 2, 0))["C"]
+        else:
+            sub = [0] * (K - 1)
+        sub[0] = 1
+        assert pvt.to_ints(ce[e]) == [0, 0] + sub[:K - 1], f"edge {e}"
+    assert exact_column_sums(ce) == [math.comb(k, 2) * C[k] for k in range(K + 1)]
+
+
+# ---------------------------------------------------------------- errors
+
+def test_errors(pvt):
+    import torch
+    rp, col = graphs.complete(10)
+    dag = gpu_dag(pvt, rp, col)
+    with pytest.raises(pvt.PivoterError) as ei:
+        dag.count_global(W=0)
+    assert ei.value.status == 1
+    with pytest.raises(pvt.PivoterError) as ei:
+        dag.count_global(kmax=-1)
+    assert ei.value.status == 1
+    big_rp, big_col = graphs.complete(70)  # alpha 69: needs 2 words
+    dag2 = gpu_dag(pvt, big_rp, big_col)
+    with pytest.raises(pvt.PivoterError) as ei:
+        dag2.count_global(W=1)
+    assert ei.value.status == 4
+    # an asymmetric CSR is refused by validation (all indices in range)
+    bad_rp = np.array([0, 2, 3, 4], dtype=np.int64)
+    bad_col = np.array([1, 2, 0, 1], dtype=np.uint32)  # 0->2 present, 2->0 missing
+    with pytest.raises(pvt.PivoterError) as ei:
+        gpu_dag(pvt, bad_rp, bad_col, validate=True)
+    assert ei.value.status == 2
+    # a self-loop, an unsorted row
+    for rp2, col2 in [(np.array([0, 2, 3], np.int64), np.array([0, 1, 0], np.uint32)),
+                      (np.array([0, 2, 3, 4], np.int64), np.array([2, 1, 0, 0], np.uint32))]:
+        with pytest.raises(pvt.PivoterError) as ei:
+            gpu_dag(pvt, rp2, col2, validate=True)
+        assert ei.value.status == 2
+    # the library stays usable afterwards
+    assert pvt.to_ints(dag.count_global())[3] == math.comb(10, 3)
+    torch.cuda.synchronize()
