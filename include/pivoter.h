@@ -143,6 +143,24 @@ pvt_status pvt_dag_stats(const pvt_dag *dag, pvt_stats *out);
 /* Enable (1) or disable (0) per-phase device timing with CUDA events. */
 pvt_status pvt_dag_set_profiling(pvt_dag *dag, int32_t enable);
 
+/*
+ * Launch policy of the walk kernels (no counterpart in the paper, whose
+ * parallel variant gives each thread whole roots, Sec. 4 "Parallel version").
+ *   persistent  1 (default): per out-degree class, a grid sized to the GPU
+ *               whose warps take roots from a device work queue (largest
+ *               out-degree first); 0: the plain form, one warp per root and
+ *               one launch per class.
+ *   chunk       roots taken per queue access in the <=32 class (1..32,
+ *               default 4); ignored by the plain form.
+ */
+typedef struct pvt_policy {
+    int32_t persistent;
+    int32_t chunk;
+} pvt_policy;
+
+/* Set the launch policy for later count calls on this dag. */
+pvt_status pvt_dag_set_policy(pvt_dag *dag, const pvt_policy *policy);
+
 /* Release a pvt_dag and all its device memory (NULL is ignored). */
 void pvt_dag_free(pvt_dag *dag);
 

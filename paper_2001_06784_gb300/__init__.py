@@ -96,6 +96,12 @@ class Dag:
                     launches=st.launches, roots=list(st.roots), class_words=list(st.class_words),
                     ms=dict(zip(self.PHASES, list(st.ms))))
 
+    def set_policy(self, persistent: bool = True, chunk: int = 4):
+        """Launch policy of the walk kernels: persistent warps with a device
+        work queue (default) or the plain one-warp-per-root form."""
+        pol = _lib.Policy(1 if persistent else 0, int(chunk))
+        _lib.check(_lib.lib().pvt_dag_set_policy(self._h, ctypes.byref(pol)))
+
     def set_profiling(self, on: bool):
         _lib.check(_lib.lib().pvt_dag_set_profiling(self._h, 1 if on else 0))
 

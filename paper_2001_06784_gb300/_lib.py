@@ -26,9 +26,14 @@ class Stats(ctypes.Structure):
                 ("roots", ctypes.c_uint64 * 6), ("class_words", ctypes.c_uint64 * 6),
                 ("ms", ctypes.c_float * 8)]
 
+class Policy(ctypes.Structure):
+    """pvt_policy (include/pivoter.h)."""
+    _fields_ = [("persistent", ctypes.c_int32), ("chunk", ctypes.c_int32)]
+
+
 # every symbol include/pivoter.h declares
 EXPORTS = ("pvt_orient", "pvt_dag_info", "pvt_count_global", "pvt_count_local_vertex",
-           "pvt_count_local_edge", "pvt_dag_stats", "pvt_dag_set_profiling", "pvt_dag_free",
+           "pvt_count_local_edge", "pvt_dag_stats", "pvt_dag_set_profiling", "pvt_dag_set_policy", "pvt_dag_free",
            "pvt_last_error")
 
 
@@ -56,6 +61,8 @@ def load(path: str = LIB_PATH):
     lib.pvt_dag_stats.argtypes = [vp, ctypes.POINTER(Stats)]
     lib.pvt_dag_set_profiling.restype = i32
     lib.pvt_dag_set_profiling.argtypes = [vp, i32]
+    lib.pvt_dag_set_policy.restype = i32
+    lib.pvt_dag_set_policy.argtypes = [vp, ctypes.POINTER(Policy)]
     lib.pvt_dag_free.restype = None
     lib.pvt_dag_free.argtypes = [vp]
     lib.pvt_last_error.restype = ctypes.c_char_p

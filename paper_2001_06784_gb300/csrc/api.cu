@@ -81,6 +81,12 @@ static void dag_release(pvt_dag *g)
     cudaFree(g->d_q);
     cudaFree(g->hist.p);
     cudaFree(g->binom.p);
+    for (int c = 0; c < NCLASS; ++c) {
+        cudaFree(g->rootbuf[c].p);
+        cudaFree(g->qframes[c].p);
+        cudaFree(g->qready[c].p);
+    }
+    cudaFree(g->qctl);
     cudaFree(g->d_stats);
     if (g->h_err) cudaFreeHost(g->h_err);
     if (g->h_stats) cudaFreeHost(g->h_stats);
@@ -115,6 +121,7 @@ pvt_status pvt_orient(int64_t n, int64_t nnz, const int64_t *row_ptr, const uint
     if (e == cudaSuccess) e = cudaMalloc(&g->d_err, sizeof(unsigned));
     if (e == cudaSuccess) e = cudaMalloc(&g->d_q, 16 * sizeof(unsigned));
     if (e == cudaSuccess) e = cudaMalloc(&g->d_stats, 16 * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMalloc(&g->qctl, NCLASS * 8 * sizeof(uint32_t));
     for (int i = 0; i < 8 && e == cudaSuccess; ++i) {
         e = cudaEventCreate(&g->ev_t0[i]);
         if (e == cudaSuccess) e = cudaEventCreate(&g->ev_t1[i]);
@@ -202,6 +209,17 @@ pvt_status pvt_dag_set_profiling(pvt_dag *dag, int32_t enable)
         return PVT_EINVAL;
     }
     dag->profiling = enable != 0;
+    return PVT_OK;
+}
+
+pvt_status pvt_dag_set_policy(pvt_dag *dag, const pvt_policy *policy)
+{
+    if (!dag || !policy || (policy->persistent != 0 && policy->persistent != 1) || policy->chunk < 1 ||
+        policy->chunk > 32) {
+        set_error("pvt_dag_set_policy: invalid argument");
+        return PVT_EINVAL;
+    }
+    dag->policy = *policy;
     return PVT_OK;
 }
 

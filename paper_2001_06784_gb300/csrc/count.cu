@@ -12,9 +12,10 @@
 //      ties: lowest member index), the pivot child is N(S,p) with p+1, and the
 //      non-neighbours v_1 < ... < v_l of the pivot give hold children
 //      N(S,v_i) \ {v_1..v_{i-1}} with h+1 (Alg. 1 hold step).  A node whose S
-//      is a clique has a single root-to-leaf continuation (every further
-//      pivot is adjacent to all of S), so it is closed at once as a leaf with
-//      p + |S| pivot links.  At most d+1 frames are ever live: a node of size
+//      is a clique (every member has |S|-1 neighbours in S) has a single
+//      root-to-leaf continuation -- each further pivot is adjacent to all of
+//      S, so there are no hold children -- and is closed at once as a leaf
+//      with p + |S| pivot links.  At most d+1 frames are ever live: a node of size
 //      s with l non-neighbours pushes l+1 children, each of size <= s-1-l.
 //   3. tallies every leaf (h = |H(T)|, p = |P(T)|, Alg. 2):
 //        global  : a 64-bit histogram over (h, p); the counts
@@ -108,7 +109,20 @@ struct CountArgs {
     unsigned *err;
     unsigned long long *stats;  // [0] nodes, [1] leaves, [2] pivot words, [3 + class] words
     int cls;                    // out-degree class of the launch
+    unsigned chunk;             // roots per queue access (persistent form)
+    // subtree splitting (heavy classes, global counts)
+    uint32_t *rootbuf;          // [nroots][32*NW][NW] adjacency rows, published per root
+    uint32_t *qframes;          // [qcap][NW+3] donated frames: root index, d, (h<<16)|p, S
+    uint32_t *qready;           // [qcap] 1 once a frame is written
+    uint32_t *qctl;             // [0] head [1] tail [2] outstanding items [3] next root [4] idle warps
+    unsigned qcap;
 };
+
+constexpr unsigned long long SPLIT_IDLE_LIMIT_NS = 20000000000ull;  // 20 s without progress
+constexpr unsigned long long SPLIT_READY_LIMIT_NS = 1000000000ull;  // 1 s for a claimed frame
+constexpr unsigned QCAP_MARGIN = 16384;  // queue slots kept free (> concurrent donors)
+
+__device__ __forceinline__ unsigned vload(const unsigned *p) { return *(const volatile unsigned *)p; }
 
 struct WalkCounters {
     unsigned long long nodes = 0, leaves = 0, words = 0;
@@ -215,15 +229,33 @@ __device__ void local_leaf(WarpWork<NW> &Wk, const CountArgs &A, int lane, uint3
 
 // ---------------------------------------------------------- one root
 
-template <int NW, int MODE, bool SHIST>
+// One walk item: a whole root r (frame == nullptr), or a frame of root qi's
+// subtree that another warp donated (split form).
+template <int NW, int MODE, bool SHIST, bool SPLIT>
 __device__ void walk_root(WarpWork<NW> &Wk, unsigned long long *shist, const CountArgs &A, int lane,
-                          uint32_t r, WalkCounters &wc)
+                          uint32_t r, WalkCounters &wc, unsigned qi = 0, const uint32_t *frame = nullptr)
 {
     constexpr int D = WarpWork<NW>::D;
     constexpr int RS = WarpWork<NW>::RS;
     constexpr bool REG = NW <= 4;  // keep this lane's adjacency rows in registers
-    const int64_t rbeg = A.orow[r];
-    const int d = (int)(A.orow[r + 1] - rbeg);
+    int64_t rbeg = 0;
+    int d = 0;
+    uint32_t S[NW];
+    int h = 1, p = 0;
+    if (SPLIT && frame) {
+        // ---- donated frame: adjacency rows come from the root's published copy
+        d = (int)__ldcg(frame + 1);
+        const uint32_t hp0 = __ldcg(frame + 2);
+        h = (int)(hp0 >> 16);
+        p = (int)(hp0 & 0xFFFFu);
+#pragma unroll
+        for (int w = 0; w < NW; ++w) S[w] = __ldcg(frame + 3 + w);
+        const uint32_t *src = A.rootbuf + (size_t)qi * D * NW;
+        for (int t = lane; t < d * NW; t += 32) Wk.adj[(t / NW) * RS + (t % NW)] = __ldcg(src + t);
+        __syncwarp();
+    } else {
+    rbeg = A.orow[r];
+    d = (int)(A.orow[r + 1] - rbeg);
     if (d > D) {
         if (lane == 0) atomicOr(A.err, DERR_RANGE);
         return;
@@ -274,6 +306,19 @@ __device__ void walk_root(WarpWork<NW> &Wk, unsigned long long *shist, const Cou
         }
     }
     __syncwarp();
+    if (SPLIT) {
+        // publish the adjacency rows so that donated frames can be walked anywhere
+        uint32_t *dst = A.rootbuf + (size_t)qi * D * NW;
+        for (int t = lane; t < d * NW; t += 32) dst[t] = Wk.adj[(t / NW) * RS + (t % NW)];
+        __threadfence();
+        __syncwarp();
+    }
+#pragma unroll
+    for (int w = 0; w < NW; ++w) {
+        int bits = d - 32 * w;
+        S[w] = bits >= 32 ? FULL : (bits <= 0 ? 0u : ((1u << bits) - 1u));
+    }
+    }
 
     uint32_t myrow[REG ? NW : 1][REG ? NW : 1];
     if (REG) {
@@ -290,36 +335,24 @@ __device__ void walk_root(WarpWork<NW> &Wk, unsigned long long *shist, const Cou
         return Wk.adj[(j * 32 + lane) * RS + w];
     };
 
-    // ---- 2. depth-first walk
-    if (lane == 0) {
-#pragma unroll
-        for (int w = 0; w < NW; ++w) {
-            int bits = d - 32 * w;
-            Wk.stk[w] = bits >= 32 ? FULL : (bits <= 0 ? 0u : ((1u << bits) - 1u));
-        }
-        Wk.hp[0] = (1u << 16);
-        if (MODE != MODE_GLOBAL) { Wk.lk[0] = 0; Wk.path[0] = (uint16_t)d; }
-    }
-    int top = 1;
-    __syncwarp();
-    while (top > 0) {
-        --top;
-        uint32_t S[NW];
-#pragma unroll
-        for (int w = 0; w < NW; ++w) S[w] = Wk.stk[top * NW + w];
-        const uint32_t hp = Wk.hp[top];
-        const int h = (int)(hp >> 16), p = (int)(hp & 0xFFFFu);
+    // ---- 2. depth-first walk.  The current node lives in registers; hold
+    // children go to the stack and the walk continues straight into the
+    // pivot child, so a pivot chain costs no stack traffic.
+    int top = 0, bot = 0;  // live frames: stk[bot..top); donations leave from the bottom
+    unsigned tick = 0;
+    uint16_t link = 0;
+    if (MODE != MODE_GLOBAL && lane == 0) Wk.path[0] = (uint16_t)d;
+    for (;;) {
         const int depth = h + p - 1;
-        if (MODE != MODE_GLOBAL) {
-            uint16_t l = Wk.lk[top];
-            __syncwarp();
-            if (lane == 0 && depth > 0) Wk.path[depth] = l;
+        if (MODE != MODE_GLOBAL && depth > 0) {
+            if (lane == 0) Wk.path[depth] = link;
             __syncwarp();
         }
         int s = 0;
 #pragma unroll
         for (int w = 0; w < NW; ++w) s += __popc(S[w]);
         wc.nodes++;
+        bool closed = true;
         if (s == 0) {
             wc.leaves++;
             if (MODE == MODE_GLOBAL) {
@@ -330,81 +363,129 @@ __device__ void walk_root(WarpWork<NW> &Wk, unsigned long long *shist, const Cou
             } else {
                 local_leaf<NW, MODE>(Wk, A, lane, r, rbeg, d, h, p, depth, nullptr);
             }
-            __syncwarp();
-            continue;
-        }
-        // pivot: most neighbours inside S, ties -> lowest member index
-        uint32_t best = 0;
-#pragma unroll
-        for (int j = 0; j < NW; ++j) {
-            if ((S[j] >> lane) & 1u) {
-                uint32_t c = 0;
-#pragma unroll
-                for (int w = 0; w < NW; ++w) c += __popc(row(j, w) & S[w]);
-                uint32_t key = ((c + 1u) << 10) | (1023u - (uint32_t)(j * 32 + lane));
-                best = max(best, key);
-            }
-        }
-        best = __reduce_max_sync(FULL, best);
-        wc.words += (unsigned long long)s * NW;
-        const int piv = 1023 - (int)(best & 1023u);
-        const int cmax = (int)(best >> 10) - 1;
-        if (cmax == s - 1) {
-            // S is a clique: one leaf with |S| more pivot links
-            wc.leaves++;
-            if (MODE == MODE_GLOBAL) {
-                if (lane == 0) {
-                    if (SHIST) atomicAdd(&shist[h * (D + 1) + p + s], 1ull);
-                    else atomicAdd(&A.hist[(size_t)h * A.hstride + p + s], 1ull);
-                }
-            } else {
-                local_leaf<NW, MODE>(Wk, A, lane, r, rbeg, d, h, p + s, depth, S);
-            }
-            __syncwarp();
-            continue;
-        }
-        uint32_t R[NW];
-        int nR = 0;
-#pragma unroll
-        for (int w = 0; w < NW; ++w) {
-            R[w] = S[w] & ~Wk.adj[piv * RS + w];
-            if (w == (piv >> 5)) R[w] &= ~(1u << (piv & 31));
-            nR += __popc(R[w]);
-        }
-        const bool hold_ok = h + 1 <= A.kmax;
-        const int npush = 1 + (hold_ok ? nR : 0);
-        if (top + npush > D + 1) {
-            if (lane == 0) atomicOr(A.err, DERR_STACK);
-            return;
-        }
-        __syncwarp();  // every lane has read frame `top`
-        if (lane == 0) {
-#pragma unroll
-            for (int w = 0; w < NW; ++w) Wk.stk[top * NW + w] = Wk.adj[piv * RS + w] & S[w];
-            Wk.hp[top] = ((uint32_t)h << 16) | (uint32_t)(p + 1);
-            if (MODE != MODE_GLOBAL) Wk.lk[top] = (uint16_t)(LINK_PIVOT | piv);
-        }
-        if (hold_ok) {
-            int before = 0;
+        } else {
+            // pivot: most neighbours inside S, ties -> lowest member index; the
+            // degree sum tells whether S is a clique (every member has s-1)
+            uint32_t best = 0, dsum = 0;
 #pragma unroll
             for (int j = 0; j < NW; ++j) {
-                if ((R[j] >> lane) & 1u) {
-                    const uint32_t low = (1u << lane) - 1u;
-                    const int f = top + 1 + before + __popc(R[j] & low);
+                if ((S[j] >> lane) & 1u) {
+                    uint32_t c = 0;
 #pragma unroll
-                    for (int w = 0; w < NW; ++w) {
-                        uint32_t below = w < j ? R[w] : (w == j ? (R[j] & low) : 0u);
-                        Wk.stk[f * NW + w] = row(j, w) & S[w] & ~below;
-                    }
-                    Wk.hp[f] = ((uint32_t)(h + 1) << 16) | (uint32_t)p;
-                    if (MODE != MODE_GLOBAL) Wk.lk[f] = (uint16_t)(j * 32 + lane);
+                    for (int w = 0; w < NW; ++w) c += __popc(row(j, w) & S[w]);
+                    uint32_t key = ((c + 1u) << 10) | (1023u - (uint32_t)(j * 32 + lane));
+                    best = max(best, key);
+                    dsum += c;
                 }
-                before += __popc(R[j]);
+            }
+            best = __reduce_max_sync(FULL, best);
+            dsum = __reduce_add_sync(FULL, dsum);
+            wc.words += (unsigned long long)s * NW;
+            const int piv = 1023 - (int)(best & 1023u);
+            if (dsum == (uint32_t)s * (uint32_t)(s - 1)) {
+                // S is a clique: one leaf with |S| more pivot links
+                wc.leaves++;
+                if (MODE == MODE_GLOBAL) {
+                    if (lane == 0) {
+                        if (SHIST) atomicAdd(&shist[h * (D + 1) + p + s], 1ull);
+                        else atomicAdd(&A.hist[(size_t)h * A.hstride + p + s], 1ull);
+                    }
+                } else {
+                    local_leaf<NW, MODE>(Wk, A, lane, r, rbeg, d, h, p + s, depth, S);
+                }
+            } else {
+                closed = false;
+                uint32_t R[NW], P[NW];
+                int nR = 0;
+#pragma unroll
+                for (int w = 0; w < NW; ++w) {
+                    const uint32_t a = Wk.adj[piv * RS + w];
+                    P[w] = a & S[w];
+                    R[w] = S[w] & ~a;
+                    if (w == (piv >> 5)) R[w] &= ~(1u << (piv & 31));
+                    nR += __popc(R[w]);
+                }
+                if (nR > 0 && h + 1 <= A.kmax) {
+                    if (SPLIT && bot > 0 && top + nR > D + 1) {
+                        // compact the live frames down to the stack base
+                        __syncwarp();
+                        for (int t = lane; t < (top - bot) * NW; t += 32) Wk.stk[t] = Wk.stk[bot * NW + t];
+                        for (int t = lane; t < top - bot; t += 32) Wk.hp[t] = Wk.hp[bot + t];
+                        top -= bot;
+                        bot = 0;
+                        __syncwarp();
+                    }
+                    if (top + nR > D + 1) {
+                        if (lane == 0) atomicOr(A.err, DERR_STACK);
+                        return;
+                    }
+                    __syncwarp();  // every lane is done reading the last popped frame
+                    int before = 0;
+#pragma unroll
+                    for (int j = 0; j < NW; ++j) {
+                        if ((R[j] >> lane) & 1u) {
+                            const uint32_t low = (1u << lane) - 1u;
+                            const int f = top + before + __popc(R[j] & low);
+#pragma unroll
+                            for (int w = 0; w < NW; ++w) {
+                                uint32_t below = w < j ? R[w] : (w == j ? (R[j] & low) : 0u);
+                                Wk.stk[f * NW + w] = row(j, w) & S[w] & ~below;
+                            }
+                            Wk.hp[f] = ((uint32_t)(h + 1) << 16) | (uint32_t)p;
+                            if (MODE != MODE_GLOBAL) Wk.lk[f] = (uint16_t)(j * 32 + lane);
+                        }
+                        before += __popc(R[j]);
+                    }
+                    top += nR;
+                    __syncwarp();  // pushed frames visible to every lane
+                    if (SPLIT && ((++tick & 15u) == 0u)) {
+                        // donate the oldest pending frames (largest subtrees) to idle warps
+                        int ndon = 0;
+                        if (lane == 0 && top - bot >= 2 && vload(A.qctl + 4) > 0) {
+                            const unsigned tail = vload(A.qctl + 1), head = vload(A.qctl + 0);
+                            if (tail + QCAP_MARGIN < A.qcap && tail - head < 64u) ndon = min(top - bot - 1, 2);
+                        }
+                        ndon = __shfl_sync(FULL, ndon, 0);
+                        for (int k = 0; k < ndon; ++k) {
+                            const int f = bot + k;
+                            unsigned slot = 0;
+                            if (lane == 0) {
+                                atomicAdd(A.qctl + 2, 1u);  // one more outstanding item
+                                slot = atomicAdd(A.qctl + 1, 1u);
+                            }
+                            slot = __shfl_sync(FULL, slot, 0);
+                            uint32_t *fr = A.qframes + (size_t)slot * (NW + 3);
+                            if (lane < NW) fr[3 + lane] = Wk.stk[f * NW + lane];
+                            if (lane == 0) {
+                                fr[0] = qi;
+                                fr[1] = (uint32_t)d;
+                                fr[2] = Wk.hp[f];
+                            }
+                            __threadfence();
+                            __syncwarp();
+                            if (lane == 0) atomicExch(A.qready + slot, 1u);
+                        }
+                        bot += ndon;
+                    }
+                }
+                // continue into the pivot child N(S, piv)
+#pragma unroll
+                for (int w = 0; w < NW; ++w) S[w] = P[w];
+                p += 1;
+                link = (uint16_t)(LINK_PIVOT | piv);
             }
         }
-        top += npush;
-        __syncwarp();
+        if (!closed) continue;
+        if (top == bot) break;
+        --top;
+#pragma unroll
+        for (int w = 0; w < NW; ++w) S[w] = Wk.stk[top * NW + w];
+        const uint32_t hp = Wk.hp[top];
+        h = (int)(hp >> 16);
+        p = (int)(hp & 0xFFFFu);
+        if (MODE != MODE_GLOBAL) link = Wk.lk[top];
     }
+    __syncwarp();
 }
 
 template <int NW>
@@ -420,7 +501,7 @@ constexpr size_t smem_bytes()
            (SHIST ? sizeof(unsigned long long) * (32 * NW + 2) * (32 * NW + 1) : 0);
 }
 
-template <int NW, int MODE, bool SHIST, bool PERSIST>
+template <int NW, int MODE, bool SHIST, bool PERSIST, bool SPLIT>
 __global__ void __launch_bounds__(32 * warps_per_block<NW>())
     k_count(CountArgs A)
 {
@@ -435,16 +516,72 @@ __global__ void __launch_bounds__(32 * warps_per_block<NW>())
         for (int i = threadIdx.x; i < (D + 2) * (D + 1); i += blockDim.x) shist[i] = 0;
         __syncthreads();
     }
+    // roots of the light class are taken from the queue a few at a time
+    const unsigned CHUNK = NW == 1 ? A.chunk : 1u;
+    unsigned qi = 0, qend = 0;
+    if (SPLIT) {
+        // heavy roots and donated subtree frames from one device work queue
+        for (;;) {
+            int kind = 0;  // 1: donated frame in slot v, 2: fresh root v, 3: no more work
+            unsigned v = 0;
+            if (lane == 0) {
+                bool idle = false;
+                unsigned last_out = 0xFFFFFFFFu;
+                unsigned long long t0 = global_ns();
+                for (;;) {
+                    const unsigned head = vload(A.qctl + 0), tail = vload(A.qctl + 1);
+                    if (head < tail) {
+                        if (atomicCAS(A.qctl + 0, head, head + 1) == head) { kind = 1; v = head; break; }
+                        continue;
+                    }
+                    if (vload(A.qctl + 3) < A.nroots) {
+                        const unsigned rr = atomicAdd(A.qctl + 3, 1u);
+                        if (rr < A.nroots) { kind = 2; v = rr; break; }
+                    }
+                    const unsigned out = vload(A.qctl + 2);
+                    if (out == 0 || (vload(A.err) & (DERR_STACK | DERR_RANGE | DERR_TIMEOUT))) { kind = 3; break; }
+                    if (!idle) { atomicAdd(A.qctl + 4, 1u); idle = true; }
+                    if (out != last_out) { last_out = out; t0 = global_ns(); }
+                    else if (global_ns() - t0 > SPLIT_IDLE_LIMIT_NS) { atomicOr(A.err, DERR_TIMEOUT); kind = 3; break; }
+                    __nanosleep(256);
+                }
+                if (idle) atomicSub(A.qctl + 4, 1u);
+                if (kind == 1) {
+                    const unsigned long long t1 = global_ns();
+                    while (vload(A.qready + v) == 0u) {
+                        if (global_ns() - t1 > SPLIT_READY_LIMIT_NS) { atomicOr(A.err, DERR_TIMEOUT); kind = 3; break; }
+                        __nanosleep(32);
+                    }
+                    __threadfence();
+                }
+            }
+            kind = __shfl_sync(FULL, kind, 0);
+            v = __shfl_sync(FULL, v, 0);
+            if (kind == 3) break;
+            if (kind == 1) {
+                const uint32_t *fr = A.qframes + (size_t)v * (NW + 3);
+                const unsigned fq = __ldcg(fr);
+                walk_root<NW, MODE, SHIST, true>(ww[wid], shist, A, lane, 0u, wc, fq, fr);
+            } else {
+                walk_root<NW, MODE, SHIST, true>(ww[wid], shist, A, lane, A.roots[v], wc, v, nullptr);
+            }
+            __syncwarp();
+            if (lane == 0) atomicSub(A.qctl + 2, 1u);
+        }
+    } else
     for (;;) {
-        unsigned qi;
         if (PERSIST) {
-            if (lane == 0) qi = atomicAdd(A.qhead, 1u);
-            qi = __shfl_sync(FULL, qi, 0);
+            if (qi == qend) {
+                if (lane == 0) qi = atomicAdd(A.qhead, CHUNK);
+                qi = __shfl_sync(FULL, qi, 0);
+                qend = min(qi + CHUNK, A.nroots);
+            }
         } else {
             qi = blockIdx.x * WPB + wid;
         }
         if (qi >= A.nroots) break;
-        walk_root<NW, MODE, SHIST>(ww[wid], shist, A, lane, A.roots[qi], wc);
+        walk_root<NW, MODE, SHIST, false>(ww[wid], shist, A, lane, A.roots[qi], wc);
+        ++qi;
         if (!PERSIST) break;
         if (*(volatile unsigned *)A.err & (DERR_STACK | DERR_RANGE)) break;
     }
@@ -590,6 +727,15 @@ static pvt_status ensure_binom(pvt_dag *g, int W, cudaStream_t s)
     return PVT_OK;
 }
 
+// Queue counters of a split launch: head, tail, outstanding items (= roots),
+// next root, idle warps.
+__global__ void k_split_init(uint32_t *qctl, unsigned nroots)
+{
+    if (threadIdx.x < 8) qctl[threadIdx.x] = threadIdx.x == 2 ? nroots : 0u;
+}
+
+constexpr unsigned SPLIT_QCAP = 1u << 17;
+
 template <int NW, int MODE, bool SHIST>
 static pvt_status launch_class(pvt_dag *g, const CountArgs &base, int cls, cudaStream_t s)
 {
@@ -600,19 +746,43 @@ static pvt_status launch_class(pvt_dag *g, const CountArgs &base, int cls, cudaS
     A.nroots = cnt;
     A.qhead = g->d_q + cls;
     A.cls = cls;
+    A.chunk = (unsigned)g->policy.chunk;
     constexpr size_t smem = smem_bytes<NW, MODE, SHIST>();
-    auto kern = k_count<NW, MODE, SHIST, true>;
-    PVT_CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    int per_sm = 0;
-    PVT_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * warps_per_block<NW>(), smem));
-    if (per_sm < 1) {
-        set_error("count kernel cannot be resident (shared memory)");
-        return PVT_ECUDA;
+    constexpr int WPB = warps_per_block<NW>();
+    const bool persist = g->policy.persistent != 0;
+    // heavy classes of the global count split subtrees across warps
+    const bool split = persist && NW >= 2 && MODE == MODE_GLOBAL;
+    auto kern = split ? k_count<NW, MODE, SHIST, true, true>
+                      : (persist ? k_count<NW, MODE, SHIST, true, false> : k_count<NW, MODE, SHIST, false, false>);
+    if (split) {
+        pvt_status st;
+        if ((st = grow(g->rootbuf[cls], (size_t)cnt * 32 * NW * NW, s)) != PVT_OK) return st;
+        if ((st = grow(g->qframes[cls], (size_t)SPLIT_QCAP * (NW + 3), s)) != PVT_OK) return st;
+        if ((st = grow(g->qready[cls], (size_t)SPLIT_QCAP, s)) != PVT_OK) return st;
+        PVT_CK(cudaMemsetAsync(g->qready[cls].p, 0, (size_t)SPLIT_QCAP * sizeof(uint32_t), s));
+        k_split_init<<<1, 32, 0, s>>>(g->qctl + 8 * cls, cnt);
+        PVT_CK(cudaGetLastError());
+        g->stats.launches++;
+        A.rootbuf = g->rootbuf[cls].p;
+        A.qframes = g->qframes[cls].p;
+        A.qready = g->qready[cls].p;
+        A.qctl = g->qctl + 8 * cls;
+        A.qcap = SPLIT_QCAP;
     }
-    const unsigned need = (cnt + warps_per_block<NW>() - 1) / warps_per_block<NW>();
-    const unsigned grid = std::min<unsigned>((unsigned)(g->num_sms * per_sm), need);
+    PVT_CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const unsigned need = (cnt + WPB - 1) / WPB;
+    unsigned grid = need;
+    if (persist) {
+        int per_sm = 0;
+        PVT_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * WPB, smem));
+        if (per_sm < 1) {
+            set_error("count kernel cannot be resident (shared memory)");
+            return PVT_ECUDA;
+        }
+        grid = std::min<unsigned>((unsigned)(g->num_sms * per_sm), need);
+    }
     phase_begin(g, 1 + cls, s);
-    kern<<<grid, 32 * warps_per_block<NW>(), smem, s>>>(A);
+    kern<<<grid, 32 * WPB, smem, s>>>(A);
     PVT_CK(cudaGetLastError());
     phase_end(g, 1 + cls, s);
     g->stats.launches++;
@@ -660,9 +830,10 @@ static pvt_status end_call(pvt_dag *g, cudaStream_t s, const char *fn)
     return st;
 }
 
-static pvt_status check_args(pvt_dag *g, int32_t kmax, int32_t W, const void *out, const char *fn)
+static pvt_status check_args(pvt_dag *g, int32_t kmax, int32_t W, const void *out, int64_t rows,
+                             const char *fn)
 {
-    if (!g || !out || kmax < 0 || W < 1) {
+    if (!g || kmax < 0 || W < 1 || (!out && rows > 0)) {
         set_error(std::string(fn) + ": invalid argument");
         return PVT_EINVAL;
     }
@@ -680,7 +851,7 @@ static pvt_status check_args(pvt_dag *g, int32_t kmax, int32_t W, const void *ou
 
 pvt_status count_global(pvt_dag *g, int32_t kmax, int32_t W, uint64_t *C, cudaStream_t s)
 {
-    pvt_status st = check_args(g, kmax, W, C, "pvt_count_global");
+    pvt_status st = check_args(g, kmax, W, C, 1, "pvt_count_global");
     if (st != PVT_OK) return st;
     begin_call(g);
     const int hstride = g->alpha + 2;
@@ -717,7 +888,7 @@ pvt_status count_global(pvt_dag *g, int32_t kmax, int32_t W, uint64_t *C, cudaSt
 pvt_status count_local(pvt_dag *g, int32_t kmax, int32_t W, uint64_t *out, bool edge, cudaStream_t s)
 {
     const char *fn = edge ? "pvt_count_local_edge" : "pvt_count_local_vertex";
-    pvt_status st = check_args(g, kmax, W, out, fn);
+    pvt_status st = check_args(g, kmax, W, out, g ? (edge ? g->m : g->n) : 0, fn);
     if (st != PVT_OK) return st;
     begin_call(g);
     if (edge && !g->oeid) {
@@ -728,7 +899,7 @@ pvt_status count_local(pvt_dag *g, int32_t kmax, int32_t W, uint64_t *out, bool 
     const int64_t rows = edge ? g->m : g->n;
     PVT_CK(cudaMemsetAsync(g->d_err, 0, sizeof(unsigned), s));
     PVT_CK(cudaMemsetAsync(g->d_q, 0, 16 * sizeof(unsigned), s));
-    PVT_CK(cudaMemsetAsync(out, 0, (size_t)rows * (kmax + 1) * W * sizeof(uint64_t), s));
+    if (rows > 0) PVT_CK(cudaMemsetAsync(out, 0, (size_t)rows * (kmax + 1) * W * sizeof(uint64_t), s));
     PVT_CK(cudaMemsetAsync(g->d_stats, 0, 16 * sizeof(unsigned long long), s));
     unsigned long long *o = reinterpret_cast<unsigned long long *>(out);
     if (!edge && g->class_cnt[0] && kmax >= 1) {

@@ -57,6 +57,10 @@ struct pvt_dag {
     unsigned *d_q = nullptr;       // work-queue heads [16]
     unsigned *h_err = nullptr;     // pinned host copy of the status word
     pvt::DevBuf<unsigned long long> hist;   // (h, p) leaf histogram
+    // subtree splitting of heavy classes: published root adjacency, frame
+    // queue, ready flags and queue counters, one set per class
+    pvt::DevBuf<uint32_t> rootbuf[pvt::NCLASS], qframes[pvt::NCLASS], qready[pvt::NCLASS];
+    uint32_t *qctl = nullptr;                 // [NCLASS][8]
     pvt::DevBuf<unsigned long long> binom;  // multi-word Pascal table
     int binom_rows = 0, binom_W = 0;
     cudaStream_t side[pvt::NCLASS] = {};    // per-class streams for concurrent launches
@@ -66,6 +70,7 @@ struct pvt_dag {
     unsigned long long *h_stats = nullptr;  // pinned host copy
     pvt_stats stats = {};
     bool profiling = false;
+    pvt_policy policy = {1, 4};
     cudaEvent_t ev_t0[8] = {}, ev_t1[8] = {};
     bool phase_used[8] = {};
 };

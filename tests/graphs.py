@@ -35,6 +35,16 @@ def clique_minus_star(n, centre, k):
     return graphgen.from_edges(n, edges)
 
 
+def clique_minus_random(n, missing, seed):
+    """K_n without `missing` random edges: at most 2^missing maximal cliques,
+    so the SCT stays small while every root has a wide out-neighbourhood."""
+    rng = np.random.default_rng(seed)
+    iu = np.triu_indices(n, 1)
+    keep = np.ones(len(iu[0]), dtype=bool)
+    keep[rng.choice(len(keep), missing, replace=False)] = False
+    return graphgen.from_edges(n, np.stack([iu[0][keep], iu[1][keep]], axis=1))
+
+
 def gnp(n, p, seed):
     rng = np.random.default_rng(seed)
     iu = np.triu_indices(n, 1)

@@ -99,10 +99,12 @@ def test_wide_branching_global(pvt, n, centre, k):
     check_all(pvt, rp, col, vertex=True, edge=False)
 
 
-def test_wide_random_dense_global(pvt):
-    # dense random part with roots in the 65..128 class and real branching
-    rp, col = graphgen.generate(400, er_avg_deg=4.0, planted=[(1, 110, 110, 0.97), (3, 40, 70, 0.9)], seed=5)
-    check_all(pvt, rp, col, vertex=True, edge=False)
+@pytest.mark.parametrize("n,missing,vertex", [(90, 25, True), (110, 20, True), (200, 16, True), (300, 14, False),
+                                               (500, 10, False)])
+def test_wide_branching_random(pvt, n, missing, vertex):
+    # wide roots (out-degree classes up to <=512) with real branching below them
+    rp, col = graphs.clique_minus_random(n, missing, 1)
+    check_all(pvt, rp, col, vertex=vertex, edge=False)
 
 
 @pytest.mark.parametrize("kmax", [0, 1, 2, 3, 5, 9])
@@ -117,7 +119,7 @@ def test_extra_words_are_zero(pvt):
     W = dag.min_words + 2
     C = dag.count_global(W=W).cpu().numpy().view(np.uint64)
     assert (C[:, dag.min_words:] == 0).all()
-    assert pvt.to_ints(C) == [0] + [math.comb(40, k) for k in range(1, 41)] + [0]
+    assert pvt.to_ints(C) == [0] + [math.comb(40, k) for k in range(1, 41)]  # kmax = alpha + 1 = 40
 
 
 def test_workload_er2k_all(pvt):
