@@ -206,6 +206,24 @@ def main():
     C_ints = pvt.to_ints(C_words)
     omega = max(k for k, c in enumerate(C_ints) if c)
 
+    # ---- the plain form on the same steps: one warp per root, one launch per
+    # out-degree class, no work queue (what the persistent form is measured against)
+    plain_ms = []
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        dag = pvt.orient(rp_d, col_d)
+        dag.set_policy(persistent=False, chunk=1)
+        Cp = dag.count_global(kmax=kmax, W=W)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        plain_ms.append(e0.elapsed_time(e1))
+        dag.free()
+    assert pvt.to_ints(Cp) == C_ints, "plain and persistent forms differ"
+    plain_value = ws * m * len(plain_ms) / (sum(plain_ms) / 1000.0)
+
     # ---- end to end through the public API: pinned host CSR in, counts out
     C_host = torch.empty((kmax + 1, W), dtype=torch.int64).pin_memory()
     e2e_ms = []
@@ -257,11 +275,13 @@ def main():
            "e2e": {"value": e2e_value, "unit": "edges/s", "ms_per_step": e2e_s * 1000.0 / len(e2e_ms),
                    "h2d_bytes_per_step": int(rp_h.numel() * 8 + col_h.numel() * 4),
                    "d2h_bytes_per_step": int(C_host.numel() * 8)},
+           "plain": {"value": plain_value, "unit": "edges/s", "ms_per_step": float(np.mean(plain_ms)),
+                     "form": "one warp per root, one launch per out-degree class"},
            "gpu_launches": int(np.mean(launches)) * args.steps,
            "clocks": clocks,
            "phases_ms": mean_ph,
            "sct": {"nodes": walk["sct_nodes"], "leaves": walk["sct_leaves"], "pivot_words": walk["pivot_words"],
-                   "roots_per_class": walk["roots"]}}
+                   "roots_per_class": walk["roots"], "pivot_words_per_class": walk["class_words"]}}
 
     # ---- CPU baseline: the oracle, whole workload, every host core; also
     # confirms this run's counts bit-exactly

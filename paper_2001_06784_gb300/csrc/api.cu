@@ -121,7 +121,7 @@ pvt_status pvt_orient(int64_t n, int64_t nnz, const int64_t *row_ptr, const uint
     if (e == cudaSuccess) e = cudaMalloc(&g->d_err, sizeof(unsigned));
     if (e == cudaSuccess) e = cudaMalloc(&g->d_q, 16 * sizeof(unsigned));
     if (e == cudaSuccess) e = cudaMalloc(&g->d_stats, 16 * sizeof(unsigned long long));
-    if (e == cudaSuccess) e = cudaMalloc(&g->qctl, NCLASS * 8 * sizeof(uint32_t));
+    if (e == cudaSuccess) e = cudaMalloc(&g->qctl, NCLASS * 128 * sizeof(uint32_t));
     for (int i = 0; i < 8 && e == cudaSuccess; ++i) {
         e = cudaEventCreate(&g->ev_t0[i]);
         if (e == cudaSuccess) e = cudaEventCreate(&g->ev_t1[i]);

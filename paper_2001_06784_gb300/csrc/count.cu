@@ -49,6 +49,9 @@ struct WarpWork {
     uint16_t path[D + 2];        // link label at each depth of the current path
     uint16_t memH[D + 2];        // leaf members: hold vertices (local index, d = root)
     uint16_t memP[D + 2];        // leaf members: pivot vertices
+    uint32_t stk1[33];           // one-word walk of a compacted subtree: S
+    uint32_t hp1[33];            //   and (h << 16) | p
+    uint16_t cmap[32];           // compacted index -> member index
 };
 
 constexpr uint16_t LINK_PIVOT = 0x8000u;
@@ -112,17 +115,70 @@ struct CountArgs {
     unsigned chunk;             // roots per queue access (persistent form)
     // subtree splitting (heavy classes, global counts)
     uint32_t *rootbuf;          // [nroots][32*NW][NW] adjacency rows, published per root
-    uint32_t *qframes;          // [qcap][NW+3] donated frames: root index, d, (h<<16)|p, S
+    uint32_t *qframes;          // [qcap][FRAME_WORDS] donated frames (layout below)
     uint32_t *qready;           // [qcap] 1 once a frame is written
-    uint32_t *qctl;             // [0] head [1] tail [2] outstanding items [3] next root [4] idle warps
+    uint32_t *qctl;             // counters, each on its own 128-byte line (Q_* offsets)
     unsigned qcap;
 };
 
+// Work queue of a split launch.  Idle warps take a ticket (one atomicAdd on
+// the head) and wait on their own slot's ready flag; busy warps donate a
+// frame whenever tickets are ahead of the frames produced (head > tail).  A
+// warp holding a ticket leaves once no item is outstanding: then no warp can
+// produce another frame.
+constexpr int Q_HEAD = 0, Q_TAIL = 32, Q_OUT = 64, Q_ROOT = 96, QCTL_WORDS = 128;
+// Frame: [0] kind; wide (1): [1] root index, [2] d, [3] (h<<16)|p, [4..4+NW) S;
+// compacted (2): [1] (h<<16)|p, [2] S, [4..36) the 32 one-word rows.
+constexpr int FRAME_WORDS = 36;
+constexpr uint32_t FRAME_WIDE = 1u, FRAME_COMPACT = 2u;
+
+// Block-level (h, p) leaf histogram in shared memory for h < HIST_H, p < HIST_P
+// (where almost every leaf falls); other leaves go straight to the global one.
+constexpr int HIST_H = 32, HIST_P = 64;
+
+template <bool SHIST>
+__device__ __forceinline__ void tally_leaf(unsigned long long *shist, const CountArgs &A, int lane, int h, int p)
+{
+    if (lane == 0) {
+        if (SHIST && h < HIST_H && p < HIST_P) atomicAdd(&shist[h * HIST_P + p], 1ull);
+        else atomicAdd(&A.hist[(size_t)h * A.hstride + p], 1ull);
+    }
+}
+
+// Donated frames must carry enough work to pay for the queue round trip.
+constexpr int DONATE_MIN_WIDE = 16;     // members of a wide frame's label
+constexpr int DONATE_MIN_COMPACT = 14;  // members of a compacted frame's label
+
 constexpr unsigned long long SPLIT_IDLE_LIMIT_NS = 20000000000ull;  // 20 s without progress
-constexpr unsigned long long SPLIT_READY_LIMIT_NS = 1000000000ull;  // 1 s for a claimed frame
 constexpr unsigned QCAP_MARGIN = 16384;  // queue slots kept free (> concurrent donors)
 
 __device__ __forceinline__ unsigned vload(const unsigned *p) { return *(const volatile unsigned *)p; }
+
+// Lane 0: are warps waiting on tickets that no frame fills yet?
+__device__ __forceinline__ bool queue_hungry(const CountArgs &A)
+{
+    const unsigned tail = vload(A.qctl + Q_TAIL);
+    return vload(A.qctl + Q_HEAD) > tail && tail + QCAP_MARGIN < A.qcap;
+}
+
+// Reserve a frame slot (one more outstanding item); all lanes get the slot.
+__device__ __forceinline__ uint32_t *frame_reserve(const CountArgs &A, int lane, unsigned &slot)
+{
+    if (lane == 0) {
+        atomicAdd(A.qctl + Q_OUT, 1u);
+        slot = atomicAdd(A.qctl + Q_TAIL, 1u);
+    }
+    slot = __shfl_sync(FULL, slot, 0);
+    return A.qframes + (size_t)slot * FRAME_WORDS;
+}
+
+// Publish a written frame.
+__device__ __forceinline__ void frame_publish(const CountArgs &A, int lane, unsigned slot)
+{
+    __threadfence();
+    __syncwarp();
+    if (lane == 0) atomicExch(A.qready + slot, 1u);
+}
 
 struct WalkCounters {
     unsigned long long nodes = 0, leaves = 0, words = 0;
@@ -228,6 +284,163 @@ __device__ void local_leaf(WarpWork<NW> &Wk, const CountArgs &A, int lane, uint3
 }
 
 // ---------------------------------------------------------- one root
+
+// Pending wide frames of the walk that descended into a compacted subtree.
+struct Outer {
+    int *top, *bot;  // live frames stk[*bot..*top)
+    unsigned qi;     // root index within the launch
+    int d;           // root out-degree
+};
+
+// Hand wide frame f (of root qi, out-degree d) to the frame queue.
+template <int NW>
+__device__ __forceinline__ void donate_wide(WarpWork<NW> &Wk, const CountArgs &A, int lane, int f, unsigned qi,
+                                            int d)
+{
+    unsigned slot = 0;
+    uint32_t *fr = frame_reserve(A, lane, slot);
+    if (lane < NW) fr[4 + lane] = Wk.stk[f * NW + lane];
+    if (lane == 0) {
+        fr[0] = FRAME_WIDE;
+        fr[1] = qi;
+        fr[2] = (uint32_t)d;
+        fr[3] = Wk.hp[f];
+    }
+    frame_publish(A, lane, slot);
+}
+
+// Walk of a subtree in one-word bitsets: lane k holds row k of the adjacency
+// induced on the (at most 32) members of the label, S1 and (h, p) describe
+// the node.  Same pivot rule, children and leaf tally as the wide walk
+// (global counts).  In the split form, pending frames are donated to idle
+// warps as self-contained compacted frames (rows travel with the frame).
+template <int NW, bool SHIST, bool SPLIT>
+__device__ void compact_loop(WarpWork<NW> &Wk, unsigned long long *shist, const CountArgs &A, int lane,
+                             uint32_t r1, uint32_t S1, int h, int p, WalkCounters &wc, const Outer *outer)
+{
+    auto tally = [&](int hh, int pp) { tally_leaf<SHIST>(shist, A, lane, hh, pp); };
+    int top = 0, bot = 0;
+    unsigned tick = 0;
+    for (;;) {
+        const int s1 = __popc(S1);
+        wc.nodes++;
+        bool closed = true;
+        if (s1 == 0) {
+            wc.leaves++;
+            tally(h, p);
+        } else {
+            const bool in = (S1 >> lane) & 1u;
+            const uint32_t c = in ? __popc(r1 & S1) : 0u;
+            const uint32_t best = __reduce_max_sync(FULL, in ? (((c + 1u) << 5) | (31u - lane)) : 0u);
+            const uint32_t dsum = __reduce_add_sync(FULL, c);
+            wc.words += (unsigned long long)s1;
+            if (dsum == (uint32_t)s1 * (uint32_t)(s1 - 1)) {
+                wc.leaves++;
+                tally(h, p + s1);
+            } else {
+                closed = false;
+                const int piv = 31 - (int)(best & 31u);
+                const uint32_t rp = __shfl_sync(FULL, r1, piv);
+                const uint32_t R = S1 & ~rp & ~(1u << piv);
+                const int nR = __popc(R);
+                if (nR > 0 && h + 1 <= A.kmax) {
+                    if (SPLIT && bot > 0 && top + nR > 33) {
+                        __syncwarp();
+                        for (int t = lane; t < top - bot; t += 32) {
+                            Wk.stk1[t] = Wk.stk1[bot + t];
+                            Wk.hp1[t] = Wk.hp1[bot + t];
+                        }
+                        top -= bot;
+                        bot = 0;
+                        __syncwarp();
+                    }
+                    if (top + nR > 33) {
+                        if (lane == 0) atomicOr(A.err, DERR_STACK);
+                        return;
+                    }
+                    __syncwarp();
+                    if ((R >> lane) & 1u) {
+                        const uint32_t below = R & ((1u << lane) - 1u);
+                        const int f = top + __popc(below);
+                        Wk.stk1[f] = r1 & S1 & ~below;
+                        Wk.hp1[f] = ((uint32_t)(h + 1) << 16) | (uint32_t)p;
+                    }
+                    top += nR;
+                    __syncwarp();
+                    if (SPLIT && ((++tick & 15u) == 0u)) {
+                        // waiting warps get the largest pending work first: the
+                        // enclosing wide walk's oldest frame, else our oldest
+                        int ndon = 0, wide = 0;
+                        if (lane == 0 && queue_hungry(A)) {
+                            if (outer && *outer->top - *outer->bot >= 1) {
+                                int sz = 0;
+#pragma unroll
+                                for (int w = 0; w < NW; ++w) sz += __popc(Wk.stk[*outer->bot * NW + w]);
+                                wide = sz >= DONATE_MIN_WIDE;
+                            }
+                            if (!wide && top - bot >= 2 && __popc(Wk.stk1[bot]) >= DONATE_MIN_COMPACT) ndon = 1;
+                        }
+                        wide = __shfl_sync(FULL, wide, 0);
+                        ndon = __shfl_sync(FULL, ndon, 0);
+                        if (wide) {
+                            donate_wide<NW>(Wk, A, lane, *outer->bot, outer->qi, outer->d);
+                            *outer->bot += 1;
+                        } else if (ndon) {
+                            unsigned slot = 0;
+                            uint32_t *fr = frame_reserve(A, lane, slot);
+                            fr[4 + lane] = r1;
+                            if (lane == 0) {
+                                fr[0] = FRAME_COMPACT;
+                                fr[1] = Wk.hp1[bot];
+                                fr[2] = Wk.stk1[bot];
+                            }
+                            frame_publish(A, lane, slot);
+                            bot += 1;
+                        }
+                    }
+                }
+                S1 = rp & S1;
+                p += 1;
+            }
+        }
+        if (!closed) continue;
+        if (top == bot) break;
+        --top;
+        S1 = Wk.stk1[top];
+        const uint32_t hp = Wk.hp1[top];
+        h = (int)(hp >> 16);
+        p = (int)(hp & 0xFFFFu);
+    }
+    __syncwarp();
+}
+
+// Compact a node whose label S (in NW-word bitsets over the root's members)
+// has s <= 32 members: relabel them 0..s-1 in ascending order; lane k gets
+// row k of the induced adjacency -- by symmetry, the ballot over lanes j of
+// "member k is in my row" is exactly that row.
+template <int NW, bool SHIST, bool SPLIT>
+__device__ void walk_compact(WarpWork<NW> &Wk, unsigned long long *shist, const CountArgs &A, int lane,
+                             const uint32_t *S, int s, int h, int p, WalkCounters &wc, const Outer *outer)
+{
+    constexpr int RS = WarpWork<NW>::RS;
+    int before = 0;
+#pragma unroll
+    for (int w = 0; w < NW; ++w) {
+        if ((S[w] >> lane) & 1u) Wk.cmap[before + __popc(S[w] & ((1u << lane) - 1u))] = (uint16_t)(w * 32 + lane);
+        before += __popc(S[w]);
+    }
+    __syncwarp();
+    const int mj = lane < s ? Wk.cmap[lane] : 0;
+    uint32_t r1 = 0;
+    for (int k = 0; k < s; ++k) {
+        const int mk = Wk.cmap[k];
+        const bool bit = lane < s && ((Wk.adj[mj * RS + (mk >> 5)] >> (mk & 31)) & 1u);
+        const uint32_t col = __ballot_sync(FULL, bit);
+        if (lane == k) r1 = col;
+    }
+    __syncwarp();
+    compact_loop<NW, SHIST, SPLIT>(Wk, shist, A, lane, r1, s >= 32 ? FULL : ((1u << s) - 1u), h, p, wc, outer);
+}
 
 // One walk item: a whole root r (frame == nullptr), or a frame of root qi's
 // subtree that another warp donated (split form).
@@ -351,15 +564,15 @@ __device__ void walk_root(WarpWork<NW> &Wk, unsigned long long *shist, const Cou
         int s = 0;
 #pragma unroll
         for (int w = 0; w < NW; ++w) s += __popc(S[w]);
-        wc.nodes++;
         bool closed = true;
-        if (s == 0) {
+        if (NW > 1 && MODE == MODE_GLOBAL && s >= 4 && s <= 32) {
+            // small label under a wide root: finish this subtree in one-word bitsets
+            const Outer outer{&top, &bot, qi, d};
+            walk_compact<NW, SHIST, SPLIT>(Wk, shist, A, lane, S, s, h, p, wc, &outer);
+        } else if ((wc.nodes++, s == 0)) {
             wc.leaves++;
             if (MODE == MODE_GLOBAL) {
-                if (lane == 0) {
-                    if (SHIST) atomicAdd(&shist[h * (D + 1) + p], 1ull);
-                    else atomicAdd(&A.hist[(size_t)h * A.hstride + p], 1ull);
-                }
+                tally_leaf<SHIST>(shist, A, lane, h, p);
             } else {
                 local_leaf<NW, MODE>(Wk, A, lane, r, rbeg, d, h, p, depth, nullptr);
             }
@@ -386,10 +599,7 @@ __device__ void walk_root(WarpWork<NW> &Wk, unsigned long long *shist, const Cou
                 // S is a clique: one leaf with |S| more pivot links
                 wc.leaves++;
                 if (MODE == MODE_GLOBAL) {
-                    if (lane == 0) {
-                        if (SHIST) atomicAdd(&shist[h * (D + 1) + p + s], 1ull);
-                        else atomicAdd(&A.hist[(size_t)h * A.hstride + p + s], 1ull);
-                    }
+                    tally_leaf<SHIST>(shist, A, lane, h, p + s);
                 } else {
                     local_leaf<NW, MODE>(Wk, A, lane, r, rbeg, d, h, p + s, depth, S);
                 }
@@ -438,33 +648,17 @@ __device__ void walk_root(WarpWork<NW> &Wk, unsigned long long *shist, const Cou
                     }
                     top += nR;
                     __syncwarp();  // pushed frames visible to every lane
-                    if (SPLIT && ((++tick & 15u) == 0u)) {
-                        // donate the oldest pending frames (largest subtrees) to idle warps
+                    if (SPLIT && ((++tick & 7u) == 0u)) {
+                        // donate the oldest pending frame (largest subtree) to an idle warp
                         int ndon = 0;
-                        if (lane == 0 && top - bot >= 2 && vload(A.qctl + 4) > 0) {
-                            const unsigned tail = vload(A.qctl + 1), head = vload(A.qctl + 0);
-                            if (tail + QCAP_MARGIN < A.qcap && tail - head < 64u) ndon = min(top - bot - 1, 2);
+                        if (lane == 0 && top - bot >= 2) {
+                            int sz = 0;
+#pragma unroll
+                            for (int w = 0; w < NW; ++w) sz += __popc(Wk.stk[bot * NW + w]);
+                            if (sz >= DONATE_MIN_WIDE && queue_hungry(A)) ndon = 1;
                         }
                         ndon = __shfl_sync(FULL, ndon, 0);
-                        for (int k = 0; k < ndon; ++k) {
-                            const int f = bot + k;
-                            unsigned slot = 0;
-                            if (lane == 0) {
-                                atomicAdd(A.qctl + 2, 1u);  // one more outstanding item
-                                slot = atomicAdd(A.qctl + 1, 1u);
-                            }
-                            slot = __shfl_sync(FULL, slot, 0);
-                            uint32_t *fr = A.qframes + (size_t)slot * (NW + 3);
-                            if (lane < NW) fr[3 + lane] = Wk.stk[f * NW + lane];
-                            if (lane == 0) {
-                                fr[0] = qi;
-                                fr[1] = (uint32_t)d;
-                                fr[2] = Wk.hp[f];
-                            }
-                            __threadfence();
-                            __syncwarp();
-                            if (lane == 0) atomicExch(A.qready + slot, 1u);
-                        }
+                        for (int k = 0; k < ndon; ++k) donate_wide<NW>(Wk, A, lane, bot + k, qi, d);
                         bot += ndon;
                     }
                 }
@@ -498,7 +692,7 @@ template <int NW, int MODE, bool SHIST>
 constexpr size_t smem_bytes()
 {
     return sizeof(WarpWork<NW>) * warps_per_block<NW>() +
-           (SHIST ? sizeof(unsigned long long) * (32 * NW + 2) * (32 * NW + 1) : 0);
+           (SHIST ? sizeof(unsigned long long) * HIST_H * HIST_P : 0);
 }
 
 template <int NW, int MODE, bool SHIST, bool PERSIST, bool SPLIT>
@@ -506,14 +700,13 @@ __global__ void __launch_bounds__(32 * warps_per_block<NW>())
     k_count(CountArgs A)
 {
     constexpr int WPB = warps_per_block<NW>();
-    constexpr int D = 32 * NW;
     extern __shared__ __align__(16) unsigned char smem[];
     WarpWork<NW> *ww = reinterpret_cast<WarpWork<NW> *>(smem);
     unsigned long long *shist = reinterpret_cast<unsigned long long *>(ww + WPB);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     WalkCounters wc;
     if (SHIST) {
-        for (int i = threadIdx.x; i < (D + 2) * (D + 1); i += blockDim.x) shist[i] = 0;
+        for (int i = threadIdx.x; i < HIST_H * HIST_P; i += blockDim.x) shist[i] = 0;
         __syncthreads();
     }
     // roots of the light class are taken from the queue a few at a time
@@ -525,48 +718,44 @@ __global__ void __launch_bounds__(32 * warps_per_block<NW>())
             int kind = 0;  // 1: donated frame in slot v, 2: fresh root v, 3: no more work
             unsigned v = 0;
             if (lane == 0) {
-                bool idle = false;
-                unsigned last_out = 0xFFFFFFFFu;
-                unsigned long long t0 = global_ns();
-                for (;;) {
-                    const unsigned head = vload(A.qctl + 0), tail = vload(A.qctl + 1);
-                    if (head < tail) {
-                        if (atomicCAS(A.qctl + 0, head, head + 1) == head) { kind = 1; v = head; break; }
-                        continue;
-                    }
-                    if (vload(A.qctl + 3) < A.nroots) {
-                        const unsigned rr = atomicAdd(A.qctl + 3, 1u);
-                        if (rr < A.nroots) { kind = 2; v = rr; break; }
-                    }
-                    const unsigned out = vload(A.qctl + 2);
-                    if (out == 0 || (vload(A.err) & (DERR_STACK | DERR_RANGE | DERR_TIMEOUT))) { kind = 3; break; }
-                    if (!idle) { atomicAdd(A.qctl + 4, 1u); idle = true; }
-                    if (out != last_out) { last_out = out; t0 = global_ns(); }
-                    else if (global_ns() - t0 > SPLIT_IDLE_LIMIT_NS) { atomicOr(A.err, DERR_TIMEOUT); kind = 3; break; }
-                    __nanosleep(256);
+                if (vload(A.qctl + Q_ROOT) < A.nroots) {
+                    const unsigned rr = atomicAdd(A.qctl + Q_ROOT, 1u);
+                    if (rr < A.nroots) { kind = 2; v = rr; }
                 }
-                if (idle) atomicSub(A.qctl + 4, 1u);
-                if (kind == 1) {
-                    const unsigned long long t1 = global_ns();
-                    while (vload(A.qready + v) == 0u) {
-                        if (global_ns() - t1 > SPLIT_READY_LIMIT_NS) { atomicOr(A.err, DERR_TIMEOUT); kind = 3; break; }
-                        __nanosleep(32);
+                if (kind == 0) {
+                    // a ticket for the next donated frame; wait on its own slot
+                    const unsigned t = atomicAdd(A.qctl + Q_HEAD, 1u);
+                    unsigned last_out = 0xFFFFFFFFu, nap = 64;
+                    unsigned long long t0 = global_ns();
+                    for (;;) {
+                        if (t < A.qcap && vload(A.qready + t)) { kind = 1; v = t; break; }
+                        const unsigned out = vload(A.qctl + Q_OUT);
+                        if (out == 0 || (vload(A.err) & (DERR_STACK | DERR_RANGE | DERR_TIMEOUT))) { kind = 3; break; }
+                        if (out != last_out) { last_out = out; t0 = global_ns(); }
+                        else if (global_ns() - t0 > SPLIT_IDLE_LIMIT_NS) { atomicOr(A.err, DERR_TIMEOUT); kind = 3; break; }
+                        __nanosleep(nap);
+                        nap = min(nap * 2u, 2048u);
                     }
-                    __threadfence();
+                    if (kind == 1) __threadfence();
                 }
             }
             kind = __shfl_sync(FULL, kind, 0);
             v = __shfl_sync(FULL, v, 0);
             if (kind == 3) break;
             if (kind == 1) {
-                const uint32_t *fr = A.qframes + (size_t)v * (NW + 3);
-                const unsigned fq = __ldcg(fr);
-                walk_root<NW, MODE, SHIST, true>(ww[wid], shist, A, lane, 0u, wc, fq, fr);
+                const uint32_t *fr = A.qframes + (size_t)v * FRAME_WORDS;
+                if (__ldcg(fr) == FRAME_COMPACT) {
+                    const uint32_t hp0 = __ldcg(fr + 1);
+                    compact_loop<NW, SHIST, true>(ww[wid], shist, A, lane, __ldcg(fr + 4 + lane), __ldcg(fr + 2),
+                                                  (int)(hp0 >> 16), (int)(hp0 & 0xFFFFu), wc, nullptr);
+                } else {
+                    walk_root<NW, MODE, SHIST, true>(ww[wid], shist, A, lane, 0u, wc, __ldcg(fr + 1), fr + 1);
+                }
             } else {
                 walk_root<NW, MODE, SHIST, true>(ww[wid], shist, A, lane, A.roots[v], wc, v, nullptr);
             }
             __syncwarp();
-            if (lane == 0) atomicSub(A.qctl + 2, 1u);
+            if (lane == 0) atomicSub(A.qctl + Q_OUT, 1u);
         }
     } else
     for (;;) {
@@ -593,9 +782,9 @@ __global__ void __launch_bounds__(32 * warps_per_block<NW>())
     }
     if (SHIST) {
         __syncthreads();
-        for (int i = threadIdx.x; i < (D + 2) * (D + 1); i += blockDim.x) {
+        for (int i = threadIdx.x; i < HIST_H * HIST_P; i += blockDim.x) {
             unsigned long long v = shist[i];
-            if (v) atomicAdd(&A.hist[(size_t)(i / (D + 1)) * A.hstride + (i % (D + 1))], v);
+            if (v) atomicAdd(&A.hist[(size_t)(i / HIST_P) * A.hstride + (i % HIST_P)], v);
         }
     }
 }
@@ -731,7 +920,7 @@ static pvt_status ensure_binom(pvt_dag *g, int W, cudaStream_t s)
 // next root, idle warps.
 __global__ void k_split_init(uint32_t *qctl, unsigned nroots)
 {
-    if (threadIdx.x < 8) qctl[threadIdx.x] = threadIdx.x == 2 ? nroots : 0u;
+    for (int i = threadIdx.x; i < QCTL_WORDS; i += blockDim.x) qctl[i] = i == Q_OUT ? nroots : 0u;
 }
 
 constexpr unsigned SPLIT_QCAP = 1u << 17;
@@ -757,16 +946,16 @@ static pvt_status launch_class(pvt_dag *g, const CountArgs &base, int cls, cudaS
     if (split) {
         pvt_status st;
         if ((st = grow(g->rootbuf[cls], (size_t)cnt * 32 * NW * NW, s)) != PVT_OK) return st;
-        if ((st = grow(g->qframes[cls], (size_t)SPLIT_QCAP * (NW + 3), s)) != PVT_OK) return st;
+        if ((st = grow(g->qframes[cls], (size_t)SPLIT_QCAP * FRAME_WORDS, s)) != PVT_OK) return st;
         if ((st = grow(g->qready[cls], (size_t)SPLIT_QCAP, s)) != PVT_OK) return st;
         PVT_CK(cudaMemsetAsync(g->qready[cls].p, 0, (size_t)SPLIT_QCAP * sizeof(uint32_t), s));
-        k_split_init<<<1, 32, 0, s>>>(g->qctl + 8 * cls, cnt);
+        k_split_init<<<1, 128, 0, s>>>(g->qctl + QCTL_WORDS * cls, cnt);
         PVT_CK(cudaGetLastError());
         g->stats.launches++;
         A.rootbuf = g->rootbuf[cls].p;
         A.qframes = g->qframes[cls].p;
         A.qready = g->qready[cls].p;
-        A.qctl = g->qctl + 8 * cls;
+        A.qctl = g->qctl + QCTL_WORDS * cls;
         A.qcap = SPLIT_QCAP;
     }
     PVT_CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -801,9 +990,9 @@ static pvt_status launch_all(pvt_dag *g, const CountArgs &A, cudaStream_t s)
         switch (c) {
             case 1: st = launch_class<1, MODE, MODE == MODE_GLOBAL>(g, A, c, cs); break;
             case 2: st = launch_class<2, MODE, MODE == MODE_GLOBAL>(g, A, c, cs); break;
-            case 3: st = launch_class<4, MODE, false>(g, A, c, cs); break;
-            case 4: st = launch_class<8, MODE, false>(g, A, c, cs); break;
-            case 5: st = launch_class<16, MODE, false>(g, A, c, cs); break;
+            case 3: st = launch_class<4, MODE, MODE == MODE_GLOBAL>(g, A, c, cs); break;
+            case 4: st = launch_class<8, MODE, MODE == MODE_GLOBAL>(g, A, c, cs); break;
+            case 5: st = launch_class<16, MODE, MODE == MODE_GLOBAL>(g, A, c, cs); break;
         }
         PVT_CK(cudaEventRecord(g->ev_join[c], cs));
     }

@@ -60,7 +60,9 @@ __global__ void k_validate(int64_t n, int64_t nnz, const int64_t *__restrict__ r
 
 struct PeelState {
     unsigned cnt[3];      // rotating frontier sizes
-    unsigned min_deg;     // smallest residual degree among remaining vertices
+    unsigned min_deg[2];  // smallest residual degree among remaining vertices (by level parity)
+    unsigned remain[2];   // vertices not yet removed (by level parity)
+    unsigned tlen;        // tail list length
     unsigned bar_count;   // grid barrier arrivals
     unsigned bar_gen;     // grid barrier generation
     unsigned rounds;      // rounds used (diagnostic)
@@ -68,6 +70,77 @@ struct PeelState {
 };
 
 constexpr unsigned long long BARRIER_LIMIT_NS = 4000000000ull;  // 4 s
+// Once at most this many vertices remain, block 0 finishes the peel alone
+// with block-level barriers (the remaining levels mostly have tiny rounds).
+constexpr unsigned PEEL_TAIL = 1u << 12;
+
+// Level-synchronous peel of the remaining vertices L[0..len) by one block.
+__device__ void peel_tail(const int64_t *__restrict__ rp, const uint32_t *__restrict__ col, uint32_t *deg,
+                          uint32_t *rnd, uint32_t *core, uint32_t *cur, uint32_t *nxt, uint32_t *L,
+                          uint32_t *L2, unsigned len, unsigned k, unsigned round, PeelState *st)
+{
+    __shared__ unsigned s_len, s_min, s_f;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    unsigned levels = 0;
+    for (;;) {
+        // drop removed vertices from the list; smallest residual degree
+        if (threadIdx.x == 0) { s_len = 0; s_min = NOT_REMOVED; }
+        __syncthreads();
+        for (unsigned i = threadIdx.x; i < len; i += blockDim.x) {
+            const uint32_t v = L[i];
+            if (rnd[v] == NOT_REMOVED) {
+                L2[atomicAdd(&s_len, 1u)] = v;
+                atomicMin(&s_min, deg[v]);
+            }
+        }
+        __syncthreads();
+        len = s_len;
+        const unsigned md = s_min;
+        { uint32_t *t = L; L = L2; L2 = t; }
+        if (len == 0) break;
+        k = max(k, md);
+        ++levels;
+        if (threadIdx.x == 0) s_f = 0;
+        __syncthreads();
+        for (unsigned i = threadIdx.x; i < len; i += blockDim.x) {
+            const uint32_t v = L[i];
+            if (deg[v] <= k) {
+                rnd[v] = round;
+                core[v] = k;
+                cur[atomicAdd(&s_f, 1u)] = v;
+            }
+        }
+        __syncthreads();
+        unsigned fsize = s_f;
+        while (fsize) {
+            __syncthreads();
+            if (threadIdx.x == 0) s_f = 0;
+            __syncthreads();
+            for (unsigned i = warp; i < fsize; i += nwarps) {
+                const uint32_t v = cur[i];
+                for (int64_t j = rp[v] + lane; j < rp[v + 1]; j += 32) {
+                    const uint32_t u = col[j];
+                    if (rnd[u] == NOT_REMOVED) {
+                        const unsigned old = atomicSub(&deg[u], 1u);
+                        if (old == k + 1) {
+                            rnd[u] = round + 1;
+                            core[u] = k;
+                            nxt[atomicAdd(&s_f, 1u)] = u;
+                        }
+                    }
+                }
+            }
+            __syncthreads();
+            fsize = s_f;
+            ++round;
+            uint32_t *t = cur; cur = nxt; nxt = t;
+        }
+    }
+    if (threadIdx.x == 0) {
+        st->rounds = round;
+        st->levels += levels;
+    }
+}
 
 // Grid-wide barrier for a cooperative launch, with a bounded wait: on
 // timeout it sets DERR_TIMEOUT and every block leaves the kernel.
@@ -86,15 +159,19 @@ __device__ bool grid_barrier(PeelState *st, unsigned *err)
             __threadfence();
             atomicAdd(&st->bar_gen, 1u);
         } else {
+            // poll tightly first (a barrier usually completes within a few
+            // microseconds), then back off; give up after BARRIER_LIMIT_NS
             unsigned long long t0 = global_ns();
+            unsigned spins = 0;
             while (*vgen == gen) {
+                if (++spins < 4096) continue;
                 if (*(volatile unsigned *)err & DERR_TIMEOUT) { ok = 0; break; }
                 if (global_ns() - t0 > BARRIER_LIMIT_NS) {
                     atomicOr(err, DERR_TIMEOUT);
                     ok = 0;
                     break;
                 }
-                __nanosleep(64);
+                __nanosleep(32);
             }
         }
         __threadfence();
@@ -104,10 +181,10 @@ __device__ bool grid_barrier(PeelState *st, unsigned *err)
     return s_ok != 0;
 }
 
-__global__ void __launch_bounds__(512) k_peel(int64_t n, const int64_t *__restrict__ rp,
+__global__ void __launch_bounds__(1024) k_peel(int64_t n, const int64_t *__restrict__ rp,
                                               const uint32_t *__restrict__ col, uint32_t *deg,
                                               uint32_t *rnd, uint32_t *core, uint32_t *fa,
-                                              uint32_t *fb, PeelState *st, unsigned *err)
+                                              uint32_t *fb, uint32_t *tl, PeelState *st, unsigned *err)
 {
     const int lane = threadIdx.x & 31;
     const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -121,24 +198,46 @@ __global__ void __launch_bounds__(512) k_peel(int64_t n, const int64_t *__restri
     }
     if (!grid_barrier(st, err)) return;
 
-    unsigned k = 0, round = 0;
+    unsigned k = 0, round = 0, level = 0;
     uint32_t *cur = fa, *nxt = fb;
+    if (tid == 0) { st->min_deg[0] = NOT_REMOVED; st->remain[0] = 0; st->tlen = 0; }
+    if (!grid_barrier(st, err)) return;
     for (;;) {
-        // ---- level start: smallest residual degree among remaining vertices
-        if (tid == 0) { st->min_deg = NOT_REMOVED; st->cnt[round % 3] = 0; }
-        if (!grid_barrier(st, err)) return;
+        // ---- level start: smallest residual degree among remaining vertices.
+        // The counters of this level (parity) were reset during the previous
+        // level, after everyone had read them two levels ago.
+        const unsigned lp = level & 1u;
         {
-            unsigned mine = NOT_REMOVED;
+            unsigned mine = NOT_REMOVED, cntr = 0;
             for (int64_t v = tid; v < n; v += nthreads)
-                if (rnd[v] == NOT_REMOVED) mine = min(mine, deg[v]);
-            for (int o = 16; o; o >>= 1) mine = min(mine, __shfl_xor_sync(FULL, mine, o));
-            if (lane == 0 && mine != NOT_REMOVED) atomicMin(&st->min_deg, mine);
+                if (rnd[v] == NOT_REMOVED) { mine = min(mine, deg[v]); ++cntr; }
+            for (int o = 16; o; o >>= 1) {
+                mine = min(mine, __shfl_xor_sync(FULL, mine, o));
+                cntr += __shfl_xor_sync(FULL, cntr, o);
+            }
+            if (lane == 0 && mine != NOT_REMOVED) { atomicMin(&st->min_deg[lp], mine); atomicAdd(&st->remain[lp], cntr); }
         }
         if (!grid_barrier(st, err)) return;
-        unsigned md = vst->min_deg;
+        unsigned md = vst->min_deg[lp];
         if (md == NOT_REMOVED) break;  // every vertex removed
+        if (vst->remain[lp] <= PEEL_TAIL) {
+            // hand the last vertices to block 0: no grid barrier after this point
+            for (int64_t v = tid; v < n; v += nthreads)
+                if (rnd[v] == NOT_REMOVED) tl[atomicAdd(&st->tlen, 1u)] = (uint32_t)v;
+            if (!grid_barrier(st, err)) return;
+            if (blockIdx.x == 0)
+                peel_tail(rp, col, deg, rnd, core, cur, nxt, tl, tl + PEEL_TAIL, vst->tlen, k, round, st);
+            return;
+        }
         k = max(k, md);
-        if (tid == 0) st->levels++;
+        if (tid == 0) {
+            // next level's counters (last read before the previous barrier);
+            // cnt[round % 3] is already 0: the previous level ended on it
+            st->levels++;
+            st->min_deg[lp ^ 1u] = NOT_REMOVED;
+            st->remain[lp ^ 1u] = 0;
+        }
+        ++level;
         // ---- this level's first frontier: all remaining with deg <= k
         for (int64_t v = tid; v < n; v += nthreads) {
             if (rnd[v] == NOT_REMOVED && deg[v] <= k) {
@@ -436,14 +535,16 @@ pvt_status orient_build(pvt_dag *g, uint32_t flags, cudaStream_t s)
     PVT_CK(cudaMallocAsync(&fa, nb, s));
     PVT_CK(cudaMallocAsync(&fb, nb, s));
     PVT_CK(cudaMallocAsync(&pst, sizeof(PeelState) + sizeof(unsigned), s));
+    uint32_t *tl = nullptr;
+    PVT_CK(cudaMallocAsync(&tl, 2 * (size_t)PEEL_TAIL * sizeof(uint32_t), s));
     PVT_CK(cudaMallocAsync(&g->rnd, nb, s));
     PVT_CK(cudaMallocAsync(&g->core, nb, s));
     PVT_CK(cudaMemsetAsync(pst, 0, sizeof(PeelState) + sizeof(unsigned), s));
 
     // one cooperative launch: every block must be resident at once
     int per_sm = 0;
-    PVT_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_peel, 512, 0));
-    per_sm = std::min(per_sm, 2);
+    PVT_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_peel, 1024, 0));
+    per_sm = std::min(per_sm, 1);
     if (per_sm < 1) {
         set_error("pvt_orient: peel kernel cannot be resident");
         return PVT_ECUDA;
@@ -454,9 +555,9 @@ pvt_status orient_build(pvt_dag *g, uint32_t flags, cudaStream_t s)
         const uint32_t *col = g->col;
         uint32_t *rnd = g->rnd, *core = g->core;
         unsigned *err = g->d_err;
-        void *args[] = {&nn, &rp, &col, &deg, &rnd, &core, &fa, &fb, &pst, &err};
+        void *args[] = {&nn, &rp, &col, &deg, &rnd, &core, &fa, &fb, &tl, &pst, &err};
         phase_begin(g, 0, s);
-        PVT_CK(cudaLaunchCooperativeKernel((void *)k_peel, dim3(g->num_sms * per_sm), dim3(512), args,
+        PVT_CK(cudaLaunchCooperativeKernel((void *)k_peel, dim3(g->num_sms * per_sm), dim3(1024), args,
                                            0, s));
         phase_end(g, 0, s);
         g->stats.launches++;
@@ -519,6 +620,7 @@ pvt_status orient_build(pvt_dag *g, uint32_t flags, cudaStream_t s)
     PVT_CK(cudaFreeAsync(fa, s));
     PVT_CK(cudaFreeAsync(fb, s));
     PVT_CK(cudaFreeAsync(pst, s));
+    PVT_CK(cudaFreeAsync(tl, s));
     PVT_CK(cudaFreeAsync(odeg, s));
     PVT_CK(cudaFreeAsync(dhist, s));
     PVT_CK(cudaStreamSynchronize(s));

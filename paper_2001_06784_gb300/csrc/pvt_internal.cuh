@@ -60,7 +60,7 @@ struct pvt_dag {
     // subtree splitting of heavy classes: published root adjacency, frame
     // queue, ready flags and queue counters, one set per class
     pvt::DevBuf<uint32_t> rootbuf[pvt::NCLASS], qframes[pvt::NCLASS], qready[pvt::NCLASS];
-    uint32_t *qctl = nullptr;                 // [NCLASS][8]
+    uint32_t *qctl = nullptr;                 // [NCLASS][128] queue counters
     pvt::DevBuf<unsigned long long> binom;  // multi-word Pascal table
     int binom_rows = 0, binom_W = 0;
     cudaStream_t side[pvt::NCLASS] = {};    // per-class streams for concurrent launches

@@ -137,6 +137,21 @@ def test_repeat_calls_identical(pvt):
     assert a == b and (v1 == v2).all()
 
 
+@pytest.mark.parametrize("make", [lambda: graphgen.generate(3000, er_avg_deg=12.0, planted=[(6, 20, 70, 0.9)], seed=13),
+                                  lambda: graphs.clique_minus_random(200, 16, 2)])
+def test_policies_agree(pvt, make):
+    """Plain (one warp per root) and persistent (work queue, split subtrees)
+    forms give identical words, and both match the oracle."""
+    rp, col = make()
+    ref = oracle.count(rp, col)
+    dag = gpu_dag(pvt, rp, col)
+    out = {}
+    for persistent, chunk in [(True, 4), (False, 1), (True, 1), (True, 32)]:
+        dag.set_policy(persistent=persistent, chunk=chunk)
+        out[(persistent, chunk)] = pvt.to_ints(dag.count_global(kmax=ref["kmax"]))
+    assert all(v == ref["C"] for v in out.values())
+
+
 # ------------------------------------------------------------ full sizes
 
 @pytest.mark.parametrize("name", ["cl1m_m10m_b2.1_comm500", "cl500k_m8m_b2.3_clq200"])
@@ -215,8 +230,8 @@ def test_errors(pvt):
     with pytest.raises(pvt.PivoterError) as ei:
         gpu_dag(pvt, bad_rp, bad_col, validate=True)
     assert ei.value.status == 2
-    # a self-loop, an unsorted row
-    for rp2, col2 in [(np.array([0, 2, 3], np.int64), np.array([0, 1, 0], np.uint32)),
+    # self-loops, an unsorted row (even nnz, indices in range)
+    for rp2, col2 in [(np.array([0, 2, 4], np.int64), np.array([0, 1, 0, 1], np.uint32)),
                       (np.array([0, 2, 3, 4], np.int64), np.array([2, 1, 0, 0], np.uint32))]:
         with pytest.raises(pvt.PivoterError) as ei:
             gpu_dag(pvt, rp2, col2, validate=True)
