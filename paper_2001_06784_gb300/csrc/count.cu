@@ -292,6 +292,13 @@ struct Outer {
     int d;           // root out-degree
 };
 
+// Donation clock of one warp, shared by the wide and the compacted walks:
+// the queue is consulted once every DONATE_EVERY nodes.
+struct Clock {
+    unsigned nodes = 0, next = 0;
+};
+constexpr unsigned DONATE_EVERY = 16;
+
 // Hand wide frame f (of root qi, out-degree d) to the frame queue.
 template <int NW>
 __device__ __forceinline__ void donate_wide(WarpWork<NW> &Wk, const CountArgs &A, int lane, int f, unsigned qi,
@@ -316,14 +323,15 @@ __device__ __forceinline__ void donate_wide(WarpWork<NW> &Wk, const CountArgs &A
 // warps as self-contained compacted frames (rows travel with the frame).
 template <int NW, bool SHIST, bool SPLIT>
 __device__ void compact_loop(WarpWork<NW> &Wk, unsigned long long *shist, const CountArgs &A, int lane,
-                             uint32_t r1, uint32_t S1, int h, int p, WalkCounters &wc, const Outer *outer)
+                             uint32_t r1, uint32_t S1, int h, int p, WalkCounters &wc, const Outer *outer,
+                             Clock &clk)
 {
     auto tally = [&](int hh, int pp) { tally_leaf<SHIST>(shist, A, lane, hh, pp); };
     int top = 0, bot = 0;
-    unsigned tick = 0;
     for (;;) {
         const int s1 = __popc(S1);
         wc.nodes++;
+        clk.nodes++;
         bool closed = true;
         if (s1 == 0) {
             wc.leaves++;
@@ -367,7 +375,8 @@ __device__ void compact_loop(WarpWork<NW> &Wk, unsigned long long *shist, const 
                     }
                     top += nR;
                     __syncwarp();
-                    if (SPLIT && ((++tick & 15u) == 0u)) {
+                    if (SPLIT && clk.nodes >= clk.next) {
+                        clk.next = clk.nodes + DONATE_EVERY;
                         // waiting warps get the largest pending work first: the
                         // enclosing wide walk's oldest frame, else our oldest
                         int ndon = 0, wide = 0;
@@ -420,7 +429,8 @@ __device__ void compact_loop(WarpWork<NW> &Wk, unsigned long long *shist, const 
 // "member k is in my row" is exactly that row.
 template <int NW, bool SHIST, bool SPLIT>
 __device__ void walk_compact(WarpWork<NW> &Wk, unsigned long long *shist, const CountArgs &A, int lane,
-                             const uint32_t *S, int s, int h, int p, WalkCounters &wc, const Outer *outer)
+                             const uint32_t *S, int s, int h, int p, WalkCounters &wc, const Outer *outer,
+                             Clock &clk)
 {
     constexpr int RS = WarpWork<NW>::RS;
     int before = 0;
@@ -439,7 +449,8 @@ __device__ void walk_compact(WarpWork<NW> &Wk, unsigned long long *shist, const 
         if (lane == k) r1 = col;
     }
     __syncwarp();
-    compact_loop<NW, SHIST, SPLIT>(Wk, shist, A, lane, r1, s >= 32 ? FULL : ((1u << s) - 1u), h, p, wc, outer);
+    compact_loop<NW, SHIST, SPLIT>(Wk, shist, A, lane, r1, s >= 32 ? FULL : ((1u << s) - 1u), h, p, wc, outer,
+                                   clk);
 }
 
 // One walk item: a whole root r (frame == nullptr), or a frame of root qi's
@@ -448,6 +459,7 @@ template <int NW, int MODE, bool SHIST, bool SPLIT>
 __device__ void walk_root(WarpWork<NW> &Wk, unsigned long long *shist, const CountArgs &A, int lane,
                           uint32_t r, WalkCounters &wc, unsigned qi = 0, const uint32_t *frame = nullptr)
 {
+    Clock clk;
     constexpr int D = WarpWork<NW>::D;
     constexpr int RS = WarpWork<NW>::RS;
     constexpr bool REG = NW <= 4;  // keep this lane's adjacency rows in registers
@@ -552,7 +564,6 @@ __device__ void walk_root(WarpWork<NW> &Wk, unsigned long long *shist, const Cou
     // children go to the stack and the walk continues straight into the
     // pivot child, so a pivot chain costs no stack traffic.
     int top = 0, bot = 0;  // live frames: stk[bot..top); donations leave from the bottom
-    unsigned tick = 0;
     uint16_t link = 0;
     if (MODE != MODE_GLOBAL && lane == 0) Wk.path[0] = (uint16_t)d;
     for (;;) {
@@ -568,8 +579,8 @@ __device__ void walk_root(WarpWork<NW> &Wk, unsigned long long *shist, const Cou
         if (NW > 1 && MODE == MODE_GLOBAL && s >= 4 && s <= 32) {
             // small label under a wide root: finish this subtree in one-word bitsets
             const Outer outer{&top, &bot, qi, d};
-            walk_compact<NW, SHIST, SPLIT>(Wk, shist, A, lane, S, s, h, p, wc, &outer);
-        } else if ((wc.nodes++, s == 0)) {
+            walk_compact<NW, SHIST, SPLIT>(Wk, shist, A, lane, S, s, h, p, wc, &outer, clk);
+        } else if ((wc.nodes++, clk.nodes++, s == 0)) {
             wc.leaves++;
             if (MODE == MODE_GLOBAL) {
                 tally_leaf<SHIST>(shist, A, lane, h, p);
@@ -648,7 +659,8 @@ __device__ void walk_root(WarpWork<NW> &Wk, unsigned long long *shist, const Cou
                     }
                     top += nR;
                     __syncwarp();  // pushed frames visible to every lane
-                    if (SPLIT && ((++tick & 7u) == 0u)) {
+                    if (SPLIT && clk.nodes >= clk.next) {
+                        clk.next = clk.nodes + DONATE_EVERY;
                         // donate the oldest pending frame (largest subtree) to an idle warp
                         int ndon = 0;
                         if (lane == 0 && top - bot >= 2) {
@@ -746,8 +758,9 @@ __global__ void __launch_bounds__(32 * warps_per_block<NW>())
                 const uint32_t *fr = A.qframes + (size_t)v * FRAME_WORDS;
                 if (__ldcg(fr) == FRAME_COMPACT) {
                     const uint32_t hp0 = __ldcg(fr + 1);
+                    Clock clk;
                     compact_loop<NW, SHIST, true>(ww[wid], shist, A, lane, __ldcg(fr + 4 + lane), __ldcg(fr + 2),
-                                                  (int)(hp0 >> 16), (int)(hp0 & 0xFFFFu), wc, nullptr);
+                                                  (int)(hp0 >> 16), (int)(hp0 & 0xFFFFu), wc, nullptr, clk);
                 } else {
                     walk_root<NW, MODE, SHIST, true>(ww[wid], shist, A, lane, 0u, wc, __ldcg(fr + 1), fr + 1);
                 }
@@ -1110,5 +1123,6 @@ pvt_status count_local(pvt_dag *g, int32_t kmax, int32_t W, uint64_t *out, bool 
     if (st != PVT_OK) return st;
     return end_call(g, s, fn);
 }
+
 
 }  // namespace pvt
