@@ -161,6 +161,35 @@ typedef struct pvt_policy {
 /* Set the launch policy for later count calls on this dag. */
 pvt_status pvt_dag_set_policy(pvt_dag *dag, const pvt_policy *policy);
 
+/*
+ * Global counts without any device allocation.  The paper has no
+ * counterpart: this entry point exists for callers that cannot call
+ * cudaMalloc while they count -- code that runs inside a pre-sized memory
+ * arena or a framework whose allocator it cannot reach, latency paths that
+ * forbid allocation, or contexts where an allocation could block or fail.
+ * The caller passes an oriented graph and the output; all scratch (leaf
+ * histogram, Pascal table, work-queue head, status word) lives in one fixed
+ * device array of about 400 KB that the library holds on every GPU that
+ * loads it, until the process exits.
+ *   n            vertex count (host value)
+ *   orow, ocol   device CSR of an acyclic orientation: the out-neighbours of
+ *                v are ocol[orow[v] .. orow[v+1]), sorted ascending, no
+ *                self-loops; every edge of the graph in exactly one list
+ *                (any acyclic orientation gives the same counts, e.g. "keep
+ *                the neighbours with a larger id")
+ *   alpha        the largest out-degree, at most 126 (else PVT_EINVAL; a
+ *                list longer than alpha is refused with PVT_EINVAL)
+ *   kmax, W, C   as pvt_count_global; W at most 4 (else PVT_EINVAL)
+ * The first call on a device looks up the array's device address with that
+ * device current; make that first call before any stream capture.  Every
+ * call on a device shares the one array and clears what must start at zero;
+ * calls whose work overlaps on the GPU (other streams, other host threads)
+ * race on it and must be serialised by the caller.  The call returns once C
+ * is complete and checked.
+ */
+pvt_status pvt_count_global_noalloc(int64_t n, const int64_t *orow, const uint32_t *ocol, int32_t alpha,
+                                    int32_t kmax, int32_t W, uint64_t *C, void *stream);
+
 /* Release a pvt_dag and all its device memory (NULL is ignored). */
 void pvt_dag_free(pvt_dag *dag);
 

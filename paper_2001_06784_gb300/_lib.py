@@ -33,7 +33,8 @@ class Policy(ctypes.Structure):
 
 # every symbol include/pivoter.h declares
 EXPORTS = ("pvt_orient", "pvt_dag_info", "pvt_count_global", "pvt_count_local_vertex",
-           "pvt_count_local_edge", "pvt_dag_stats", "pvt_dag_set_profiling", "pvt_dag_set_policy", "pvt_dag_free",
+           "pvt_count_local_edge", "pvt_dag_stats", "pvt_dag_set_profiling", "pvt_dag_set_policy",
+           "pvt_count_global_noalloc", "pvt_dag_free",
            "pvt_last_error")
 
 
@@ -63,6 +64,8 @@ def load(path: str = LIB_PATH):
     lib.pvt_dag_set_profiling.argtypes = [vp, i32]
     lib.pvt_dag_set_policy.restype = i32
     lib.pvt_dag_set_policy.argtypes = [vp, ctypes.POINTER(Policy)]
+    lib.pvt_count_global_noalloc.restype = i32
+    lib.pvt_count_global_noalloc.argtypes = [i64, vp, vp, i32, i32, i32, vp, vp]
     lib.pvt_dag_free.restype = None
     lib.pvt_dag_free.argtypes = [vp]
     lib.pvt_last_error.restype = ctypes.c_char_p

@@ -28,6 +28,8 @@
 // Roots come from a device work queue (persistent warps) in descending
 // out-degree, one kernel instance per bitset width NW = ceil(d / 32).
 #include <algorithm>
+#include <mutex>
+#include <string>
 
 #include "pvt_internal.cuh"
 
@@ -1125,4 +1127,171 @@ pvt_status count_local(pvt_dag *g, int32_t kmax, int32_t W, uint64_t *out, bool 
 }
 
 
+// ------------------------------------------- allocation-free global count
+//
+// Some callers cannot allocate device memory when they count: code running
+// inside a pre-sized memory arena or a framework whose allocator is not
+// reachable from C, callers that forbid allocation on their latency path, or
+// contexts in which a cudaMalloc could block on other work or fail under
+// fragmentation.  pvt_count_global_noalloc serves them: the caller passes an
+// already oriented graph and the output buffer, and every piece of scratch
+// the walk needs (the (h, p) leaf histogram, the multi-word Pascal table,
+// the work-queue head and the status word) lives in the fixed device array
+// below, which the library holds on every GPU that loads it until the
+// process exits.
+
+constexpr int NOALLOC_MAX_ALPHA = 126;  // largest out-degree (bitsets of <= 4 words)
+constexpr int NOALLOC_MAX_W = 4;        // largest W (64-bit words per count)
+constexpr size_t NOALLOC_HIST = (size_t)(NOALLOC_MAX_ALPHA + 2) * (NOALLOC_MAX_ALPHA + 2);
+constexpr size_t NOALLOC_BINOM = (size_t)(NOALLOC_MAX_ALPHA + 3) * (NOALLOC_MAX_ALPHA + 4) / 2 * NOALLOC_MAX_W;
+constexpr size_t NOALLOC_CTL = 32;      // [0] queue head + status word, [1..] walk statistics
+constexpr size_t NOALLOC_WORDS = NOALLOC_HIST + NOALLOC_BINOM + NOALLOC_CTL;  // 400 KB in all
+
+static __device__ __align__(256) unsigned long long g_noalloc_scratch[NOALLOC_WORDS];
+
+// Every vertex is a root; out-degrees above `alpha` are refused (they would
+// index outside the histogram).  Same walk as k_count, global counts.
+template <int NW>
+__global__ void __launch_bounds__(32 * warps_per_block<NW>()) k_count_noalloc(CountArgs A, int alpha)
+{
+    constexpr int WPB = warps_per_block<NW>();
+    extern __shared__ __align__(16) unsigned char smem[];
+    WarpWork<NW> *ww = reinterpret_cast<WarpWork<NW> *>(smem);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    WalkCounters wc;
+    for (;;) {
+        unsigned qi = 0;
+        if (lane == 0) qi = atomicAdd(A.qhead, 1u);
+        qi = __shfl_sync(FULL, qi, 0);
+        if (qi >= A.nroots) break;
+        const int64_t d = A.orow[qi + 1] - A.orow[qi];
+        if (d < 0 || d > alpha) {
+            if (lane == 0) atomicOr(A.err, DERR_RANGE);
+            break;
+        }
+        walk_root<NW, MODE_GLOBAL, false, false>(ww[wid], nullptr, A, lane, qi, wc);
+        if (vload(A.err) & (DERR_STACK | DERR_RANGE)) break;
+    }
+    (void)WPB;
+    if (lane == 0 && wc.nodes) {
+        atomicAdd(&A.stats[0], wc.nodes);
+        atomicAdd(&A.stats[1], wc.leaves);
+        atomicAdd(&A.stats[2], wc.words);
+    }
+}
+
+template <int NW>
+static pvt_status launch_noalloc(const CountArgs &A, int alpha, int num_sms, cudaStream_t s)
+{
+    constexpr size_t smem = sizeof(WarpWork<NW>) * warps_per_block<NW>();
+    auto kern = k_count_noalloc<NW>;
+    PVT_CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    PVT_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * warps_per_block<NW>(), smem));
+    if (per_sm < 1) {
+        set_error("pvt_count_global_noalloc: walk kernel cannot be resident");
+        return PVT_ECUDA;
+    }
+    const unsigned need = (A.nroots + warps_per_block<NW>() - 1) / warps_per_block<NW>();
+    const unsigned grid = std::max(1u, std::min<unsigned>((unsigned)(num_sms * per_sm), need));
+    kern<<<grid, 32 * warps_per_block<NW>(), smem, s>>>(A, alpha);
+    PVT_CK(cudaGetLastError());
+    return PVT_OK;
+}
+
 }  // namespace pvt
+
+extern "C" pvt_status pvt_count_global_noalloc(int64_t n, const int64_t *orow, const uint32_t *ocol,
+                                               int32_t alpha, int32_t kmax, int32_t W, uint64_t *C,
+                                               void *stream)
+{
+    using namespace pvt;
+    if (n < 0 || n > 0xFFFFFFFEll || (n > 0 && !orow) || !C || kmax < 0 || alpha < 0 || W < 1) {
+        set_error("pvt_count_global_noalloc: invalid argument");
+        return PVT_EINVAL;
+    }
+    if (alpha > NOALLOC_MAX_ALPHA || W > NOALLOC_MAX_W) {
+        set_error("pvt_count_global_noalloc: alpha <= " + std::to_string(NOALLOC_MAX_ALPHA) + " and W <= " +
+                  std::to_string(NOALLOC_MAX_W) + " required (fixed scratch)");
+        return PVT_EINVAL;
+    }
+    if (W < min_words(n, alpha)) {
+        set_error("pvt_count_global_noalloc: W below the required " + std::to_string(min_words(n, alpha)));
+        return PVT_EOVERFLOW;
+    }
+    // once per device, with that device current: the device address of the
+    // scratch array (its host-side name is only a stand-in)
+    static std::mutex mu;
+    static void *scratch_of[64] = {};
+    static int sms_of[64] = {};
+    int dev = 0;
+    PVT_CK(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) {
+        set_error("pvt_count_global_noalloc: device index above 63");
+        return PVT_EINVAL;
+    }
+    void *base = nullptr;
+    int num_sms = 0;
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        if (!scratch_of[dev]) {
+            void *ptr = nullptr;
+            PVT_CK(cudaGetSymbolAddress(&ptr, g_noalloc_scratch));
+            int sms = 0;
+            PVT_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+            scratch_of[dev] = ptr;
+            sms_of[dev] = sms;
+        }
+        base = scratch_of[dev];
+        num_sms = sms_of[dev];
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    unsigned long long *hist = static_cast<unsigned long long *>(base);
+    unsigned long long *binom = hist + NOALLOC_HIST;
+    unsigned long long *ctl = binom + NOALLOC_BINOM;
+    unsigned *qhead = reinterpret_cast<unsigned *>(ctl);
+    unsigned *err = qhead + 1;
+    const int hstride = alpha + 2;
+    // the array keeps the previous call's contents: clear what must start at zero
+    PVT_CK(cudaMemsetAsync(hist, 0, (size_t)hstride * hstride * sizeof(unsigned long long), s));
+    PVT_CK(cudaMemsetAsync(ctl, 0, NOALLOC_CTL * sizeof(unsigned long long), s));
+    k_binom<<<1, 1024, 0, s>>>(binom, alpha + 3, W, err);
+    PVT_CK(cudaGetLastError());
+    if (n > 0) {
+        CountArgs A{};
+        A.orow = orow;
+        A.ocol = ocol;
+        A.nroots = (unsigned)n;
+        A.qhead = qhead;
+        A.hist = hist;
+        A.hstride = hstride;
+        A.B = binom;
+        A.W = W;
+        A.kmax = kmax;
+        A.err = err;
+        A.stats = ctl + 1;
+        const int NWn = (alpha + 31) / 32;
+        pvt_status st = NWn <= 1 ? launch_noalloc<1>(A, alpha, num_sms, s)
+                        : NWn <= 2 ? launch_noalloc<2>(A, alpha, num_sms, s)
+                                   : launch_noalloc<4>(A, alpha, num_sms, s);
+        if (st != PVT_OK) return st;
+    }
+    k_combine<<<kmax + 1, 256, 0, s>>>(hist, hstride, binom, W, kmax, reinterpret_cast<unsigned long long *>(C), err);
+    PVT_CK(cudaGetLastError());
+    unsigned herr = 0;
+    PVT_CK(cudaMemcpyAsync(&herr, err, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+    PVT_CK(cudaStreamSynchronize(s));
+    if (herr & DERR_RANGE) {
+        set_error("pvt_count_global_noalloc: an out-degree exceeds alpha");
+        return PVT_EINVAL;
+    }
+    if (herr & DERR_OVERFLOW) {
+        set_error("pvt_count_global_noalloc: multi-word overflow");
+        return PVT_EOVERFLOW;
+    }
+    if (herr) {
+        set_error("pvt_count_global_noalloc: device capacity check failed");
+        return PVT_EINTERNAL;
+    }
+    return PVT_OK;
+}
