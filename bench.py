@@ -281,7 +281,8 @@ def main():
            "clocks": clocks,
            "phases_ms": mean_ph,
            "sct": {"nodes": walk["sct_nodes"], "leaves": walk["sct_leaves"], "pivot_words": walk["pivot_words"],
-                   "roots_per_class": walk["roots"], "pivot_words_per_class": walk["class_words"]}}
+                   "roots_per_class": walk["roots"], "pivot_words_per_class": walk["class_words"]},
+           "peel": {"rounds": so["peel_rounds"], "levels": so["peel_levels"]}}
 
     # ---- CPU baseline: the oracle, whole workload, every host core; also
     # confirms this run's counts bit-exactly

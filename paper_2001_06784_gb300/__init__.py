@@ -94,7 +94,8 @@ class Dag:
         _lib.check(_lib.lib().pvt_dag_stats(self._h, ctypes.byref(st)))
         return dict(sct_nodes=st.sct_nodes, sct_leaves=st.sct_leaves, pivot_words=st.pivot_words,
                     launches=st.launches, roots=list(st.roots), class_words=list(st.class_words),
-                    ms=dict(zip(self.PHASES, list(st.ms))))
+                    ms=dict(zip(self.PHASES, list(st.ms))), peel_rounds=st.peel_rounds,
+                    peel_levels=st.peel_levels)
 
     def set_policy(self, persistent: bool = True, chunk: int = 4):
         """Launch policy of the walk kernels: persistent warps with a device

@@ -54,6 +54,7 @@ struct WarpWork {
     uint32_t stk1[33];           // one-word walk of a compacted subtree: S
     uint32_t hp1[33];            //   and (h << 16) | p
     uint16_t cmap[32];           // compacted index -> member index
+    uint32_t fbuf[36];           // copy of a donated frame taken from the queue
 };
 
 constexpr uint16_t LINK_PIVOT = 0x8000u;
@@ -117,17 +118,19 @@ struct CountArgs {
     unsigned chunk;             // roots per queue access (persistent form)
     // subtree splitting (heavy classes, global counts)
     uint32_t *rootbuf;          // [nroots][32*NW][NW] adjacency rows, published per root
-    uint32_t *qframes;          // [qcap][FRAME_WORDS] donated frames (layout below)
-    uint32_t *qready;           // [qcap] 1 once a frame is written
+    uint32_t *qframes;          // [qcap][FRAME_WORDS] ring of donated frames (layout below)
+    uint32_t *qready;           // [qcap] t+1 once the frame of ticket t is written
+    uint32_t *qdone;            // [qcap] t+1 once the frame of ticket t is copied out
     uint32_t *qctl;             // counters, each on its own 128-byte line (Q_* offsets)
-    unsigned qcap;
+    unsigned qcap;              // power of two
 };
 
-// Work queue of a split launch.  Idle warps take a ticket (one atomicAdd on
-// the head) and wait on their own slot's ready flag; busy warps donate a
-// frame whenever tickets are ahead of the frames produced (head > tail).  A
-// warp holding a ticket leaves once no item is outstanding: then no warp can
-// produce another frame.
+// Work queue of a split launch, a ring of qcap slots.  Idle warps take a
+// ticket t (one atomicAdd on the head) and wait on slot t mod qcap until its
+// ready word says t+1; busy warps donate a frame whenever tickets are ahead
+// of the frames produced (head > tail), after the slot's previous occupant
+// (ticket t - qcap) has been copied out.  A warp holding a ticket leaves once
+// no item is outstanding: then no warp can produce another frame.
 constexpr int Q_HEAD = 0, Q_TAIL = 32, Q_OUT = 64, Q_ROOT = 96, QCTL_WORDS = 128;
 // Frame: [0] kind; wide (1): [1] root index, [2] d, [3] (h<<16)|p, [4..4+NW) S;
 // compacted (2): [1] (h<<16)|p, [2] S, [4..36) the 32 one-word rows.
@@ -152,34 +155,45 @@ constexpr int DONATE_MIN_WIDE = 16;     // members of a wide frame's label
 constexpr int DONATE_MIN_COMPACT = 14;  // members of a compacted frame's label
 
 constexpr unsigned long long SPLIT_IDLE_LIMIT_NS = 20000000000ull;  // 20 s without progress
-constexpr unsigned QCAP_MARGIN = 16384;  // queue slots kept free (> concurrent donors)
+constexpr unsigned long long SPLIT_SLOT_LIMIT_NS = 2000000000ull;  // 2 s for a ring slot to free up
 
 __device__ __forceinline__ unsigned vload(const unsigned *p) { return *(const volatile unsigned *)p; }
 
 // Lane 0: are warps waiting on tickets that no frame fills yet?
 __device__ __forceinline__ bool queue_hungry(const CountArgs &A)
 {
-    const unsigned tail = vload(A.qctl + Q_TAIL);
-    return vload(A.qctl + Q_HEAD) > tail && tail + QCAP_MARGIN < A.qcap;
+    return vload(A.qctl + Q_HEAD) > vload(A.qctl + Q_TAIL);
 }
 
-// Reserve a frame slot (one more outstanding item); all lanes get the slot.
-__device__ __forceinline__ uint32_t *frame_reserve(const CountArgs &A, int lane, unsigned &slot)
+// Reserve the slot of the next frame (one more outstanding item); all lanes
+// get its ticket number t.  Returns nullptr (status set) if the slot never
+// frees up.
+__device__ __forceinline__ uint32_t *frame_reserve(const CountArgs &A, int lane, unsigned &t)
 {
+    int ok = 1;
     if (lane == 0) {
         atomicAdd(A.qctl + Q_OUT, 1u);
-        slot = atomicAdd(A.qctl + Q_TAIL, 1u);
+        t = atomicAdd(A.qctl + Q_TAIL, 1u);
+        if (t >= A.qcap) {
+            const unsigned want = t - A.qcap + 1u, slot = t & (A.qcap - 1u);
+            const unsigned long long t0 = global_ns();
+            while (vload(A.qdone + slot) != want) {
+                if (global_ns() - t0 > SPLIT_SLOT_LIMIT_NS) { atomicOr(A.err, DERR_TIMEOUT); ok = 0; break; }
+                __nanosleep(64);
+            }
+        }
     }
-    slot = __shfl_sync(FULL, slot, 0);
-    return A.qframes + (size_t)slot * FRAME_WORDS;
+    t = __shfl_sync(FULL, t, 0);
+    ok = __shfl_sync(FULL, ok, 0);
+    return ok ? A.qframes + (size_t)(t & (A.qcap - 1u)) * FRAME_WORDS : nullptr;
 }
 
 // Publish a written frame.
-__device__ __forceinline__ void frame_publish(const CountArgs &A, int lane, unsigned slot)
+__device__ __forceinline__ void frame_publish(const CountArgs &A, int lane, unsigned t)
 {
     __threadfence();
     __syncwarp();
-    if (lane == 0) atomicExch(A.qready + slot, 1u);
+    if (lane == 0) atomicExch(A.qready + (t & (A.qcap - 1u)), t + 1u);
 }
 
 struct WalkCounters {
@@ -306,8 +320,9 @@ template <int NW>
 __device__ __forceinline__ void donate_wide(WarpWork<NW> &Wk, const CountArgs &A, int lane, int f, unsigned qi,
                                             int d)
 {
-    unsigned slot = 0;
-    uint32_t *fr = frame_reserve(A, lane, slot);
+    unsigned t = 0;
+    uint32_t *fr = frame_reserve(A, lane, t);
+    if (!fr) return;
     if (lane < NW) fr[4 + lane] = Wk.stk[f * NW + lane];
     if (lane == 0) {
         fr[0] = FRAME_WIDE;
@@ -315,7 +330,7 @@ __device__ __forceinline__ void donate_wide(WarpWork<NW> &Wk, const CountArgs &A
         fr[2] = (uint32_t)d;
         fr[3] = Wk.hp[f];
     }
-    frame_publish(A, lane, slot);
+    frame_publish(A, lane, t);
 }
 
 // Walk of a subtree in one-word bitsets: lane k holds row k of the adjacency
@@ -397,16 +412,18 @@ __device__ void compact_loop(WarpWork<NW> &Wk, unsigned long long *shist, const 
                             donate_wide<NW>(Wk, A, lane, *outer->bot, outer->qi, outer->d);
                             *outer->bot += 1;
                         } else if (ndon) {
-                            unsigned slot = 0;
-                            uint32_t *fr = frame_reserve(A, lane, slot);
-                            fr[4 + lane] = r1;
-                            if (lane == 0) {
-                                fr[0] = FRAME_COMPACT;
-                                fr[1] = Wk.hp1[bot];
-                                fr[2] = Wk.stk1[bot];
+                            unsigned t = 0;
+                            uint32_t *fr = frame_reserve(A, lane, t);
+                            if (fr) {
+                                fr[4 + lane] = r1;
+                                if (lane == 0) {
+                                    fr[0] = FRAME_COMPACT;
+                                    fr[1] = Wk.hp1[bot];
+                                    fr[2] = Wk.stk1[bot];
+                                }
+                                frame_publish(A, lane, t);
+                                bot += 1;
                             }
-                            frame_publish(A, lane, slot);
-                            bot += 1;
                         }
                     }
                 }
@@ -471,12 +488,12 @@ __device__ void walk_root(WarpWork<NW> &Wk, unsigned long long *shist, const Cou
     int h = 1, p = 0;
     if (SPLIT && frame) {
         // ---- donated frame: adjacency rows come from the root's published copy
-        d = (int)__ldcg(frame + 1);
-        const uint32_t hp0 = __ldcg(frame + 2);
+        d = (int)frame[1];
+        const uint32_t hp0 = frame[2];
         h = (int)(hp0 >> 16);
         p = (int)(hp0 & 0xFFFFu);
 #pragma unroll
-        for (int w = 0; w < NW; ++w) S[w] = __ldcg(frame + 3 + w);
+        for (int w = 0; w < NW; ++w) S[w] = frame[3 + w];
         const uint32_t *src = A.rootbuf + (size_t)qi * D * NW;
         for (int t = lane; t < d * NW; t += 32) Wk.adj[(t / NW) * RS + (t % NW)] = __ldcg(src + t);
         __syncwarp();
@@ -741,8 +758,9 @@ __global__ void __launch_bounds__(32 * warps_per_block<NW>())
                     const unsigned t = atomicAdd(A.qctl + Q_HEAD, 1u);
                     unsigned last_out = 0xFFFFFFFFu, nap = 64;
                     unsigned long long t0 = global_ns();
+                    const unsigned slot = t & (A.qcap - 1u);
                     for (;;) {
-                        if (t < A.qcap && vload(A.qready + t)) { kind = 1; v = t; break; }
+                        if (vload(A.qready + slot) == t + 1u) { kind = 1; v = t; break; }
                         const unsigned out = vload(A.qctl + Q_OUT);
                         if (out == 0 || (vload(A.err) & (DERR_STACK | DERR_RANGE | DERR_TIMEOUT))) { kind = 3; break; }
                         if (out != last_out) { last_out = out; t0 = global_ns(); }
@@ -757,14 +775,23 @@ __global__ void __launch_bounds__(32 * warps_per_block<NW>())
             v = __shfl_sync(FULL, v, 0);
             if (kind == 3) break;
             if (kind == 1) {
-                const uint32_t *fr = A.qframes + (size_t)v * FRAME_WORDS;
-                if (__ldcg(fr) == FRAME_COMPACT) {
-                    const uint32_t hp0 = __ldcg(fr + 1);
+                // copy the frame out and release its ring slot at once
+                const uint32_t *fr = A.qframes + (size_t)(v & (A.qcap - 1u)) * FRAME_WORDS;
+                uint32_t *fb = ww[wid].fbuf;
+                fb[lane] = __ldcg(fr + lane);
+                if (lane < FRAME_WORDS - 32) fb[32 + lane] = __ldcg(fr + 32 + lane);
+                __syncwarp();
+                if (lane == 0) {
+                    __threadfence();
+                    atomicExch(A.qdone + (v & (A.qcap - 1u)), v + 1u);
+                }
+                if (fb[0] == FRAME_COMPACT) {
+                    const uint32_t hp0 = fb[1];
                     Clock clk;
-                    compact_loop<NW, SHIST, true>(ww[wid], shist, A, lane, __ldcg(fr + 4 + lane), __ldcg(fr + 2),
-                                                  (int)(hp0 >> 16), (int)(hp0 & 0xFFFFu), wc, nullptr, clk);
+                    compact_loop<NW, SHIST, true>(ww[wid], shist, A, lane, fb[4 + lane], fb[2], (int)(hp0 >> 16),
+                                                  (int)(hp0 & 0xFFFFu), wc, nullptr, clk);
                 } else {
-                    walk_root<NW, MODE, SHIST, true>(ww[wid], shist, A, lane, 0u, wc, __ldcg(fr + 1), fr + 1);
+                    walk_root<NW, MODE, SHIST, true>(ww[wid], shist, A, lane, 0u, wc, fb[1], fb + 1);
                 }
             } else {
                 walk_root<NW, MODE, SHIST, true>(ww[wid], shist, A, lane, A.roots[v], wc, v, nullptr);
@@ -962,14 +989,15 @@ static pvt_status launch_class(pvt_dag *g, const CountArgs &base, int cls, cudaS
         pvt_status st;
         if ((st = grow(g->rootbuf[cls], (size_t)cnt * 32 * NW * NW, s)) != PVT_OK) return st;
         if ((st = grow(g->qframes[cls], (size_t)SPLIT_QCAP * FRAME_WORDS, s)) != PVT_OK) return st;
-        if ((st = grow(g->qready[cls], (size_t)SPLIT_QCAP, s)) != PVT_OK) return st;
-        PVT_CK(cudaMemsetAsync(g->qready[cls].p, 0, (size_t)SPLIT_QCAP * sizeof(uint32_t), s));
+        if ((st = grow(g->qready[cls], (size_t)SPLIT_QCAP * 2, s)) != PVT_OK) return st;
+        PVT_CK(cudaMemsetAsync(g->qready[cls].p, 0, (size_t)SPLIT_QCAP * 2 * sizeof(uint32_t), s));
         k_split_init<<<1, 128, 0, s>>>(g->qctl + QCTL_WORDS * cls, cnt);
         PVT_CK(cudaGetLastError());
         g->stats.launches++;
         A.rootbuf = g->rootbuf[cls].p;
         A.qframes = g->qframes[cls].p;
         A.qready = g->qready[cls].p;
+        A.qdone = g->qready[cls].p + SPLIT_QCAP;
         A.qctl = g->qctl + QCTL_WORDS * cls;
         A.qcap = SPLIT_QCAP;
     }

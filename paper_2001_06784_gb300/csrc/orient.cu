@@ -574,11 +574,15 @@ pvt_status orient_build(pvt_dag *g, uint32_t flags, cudaStream_t s)
     g->stats.launches += 4;
     if (st != PVT_OK) return st;
     unsigned alpha = 0;
+    PeelState hst{};
+    PVT_CK(cudaMemcpyAsync(&hst, pst, sizeof(PeelState), cudaMemcpyDeviceToHost, s));
     PVT_CK(cudaMemcpyAsync(&alpha, d_alpha, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
     PVT_CK(cudaStreamSynchronize(s));
     st = check_device(g, s, "pvt_orient: peeling");
     if (st != PVT_OK) return st;
     g->alpha = (int32_t)alpha;
+    g->stats.peel_rounds = hst.rounds;
+    g->stats.peel_levels = hst.levels;
     if (g->alpha > MAX_ALPHA) {
         set_error("pvt_orient: degeneracy " + std::to_string(alpha) + " above the supported " +
                   std::to_string(MAX_ALPHA));
