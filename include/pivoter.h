@@ -135,7 +135,7 @@ typedef struct pvt_stats {
     uint64_t roots[6];      /* roots per out-degree class (0, <=32, ..., <=512) */
     uint64_t class_words[6];/* pivot_words split by out-degree class */
     float ms[8];
-    uint32_t peel_rounds;   /* orient: rounds of the level-synchronous peel */
+    uint32_t peel_rounds;   /* orient: grid-wide barriers of the peel */
     uint32_t peel_levels;   /* orient: distinct core levels visited */
 } pvt_stats;
 

@@ -1,16 +1,12 @@
 // Degeneracy orientation on the device (Lemma degen, Sec. 3.2; Alg. 1 step 1).
 //
 // 1. Optional CSR validation (simple undirected graph, Sec. 3.1).
-// 2. Level-synchronous k-core peeling in one cooperative kernel: at level k,
-//    every remaining vertex whose residual degree is <= k is removed in the
-//    current round; removals lower their neighbours' residual degrees, and
-//    neighbours that reach k join the next round.  When a level empties, k
-//    rises to the smallest remaining residual degree.  A vertex removed in
-//    round t had at most k <= alpha neighbours not removed before round t.
-// 3. The orientation u -> v iff (round[u], u) < (round[v], v): every
-//    out-neighbour of v was still present when v was removed, so every
-//    out-degree is at most the degeneracy.  Out-lists keep the CSR's
-//    ascending-id order.
+// 2. k-core peeling in one cooperative kernel, exact by level (core numbers
+//    are exact), asynchronous within a level (see k_peel): each vertex gets a
+//    unique removal time rnd[v].
+// 3. The orientation u -> v iff rnd[u] < rnd[v]: a vertex's later
+//    neighbours number at most its level k <= alpha, so every out-degree is
+//    at most the degeneracy.  Out-lists keep the CSR's ascending-id order.
 // 4. Roots grouped by out-degree class (bitset width), largest first.
 #include <cooperative_groups.h>
 
@@ -58,89 +54,26 @@ __global__ void k_validate(int64_t n, int64_t nnz, const int64_t *__restrict__ r
 
 // --------------------------------------------------------------- peeling
 
+// Shared state of the peel.  Counters that many warps touch sit on their own
+// 128-byte lines.
 struct PeelState {
-    unsigned cnt[3];      // rotating frontier sizes
+    unsigned head;        // next claim on the removal queue
+    unsigned pad0[31];
+    unsigned tail;        // vertices pushed onto the removal queue so far
+    unsigned pad1[31];
+    unsigned pending;     // pushed but not yet processed (this level)
+    unsigned pad2[31];
     unsigned min_deg[2];  // smallest residual degree among remaining vertices (by level parity)
     unsigned remain[2];   // vertices not yet removed (by level parity)
-    unsigned tlen;        // tail list length
     unsigned bar_count;   // grid barrier arrivals
     unsigned bar_gen;     // grid barrier generation
-    unsigned rounds;      // rounds used (diagnostic)
+    unsigned rounds;      // grid barriers passed (diagnostic)
     unsigned levels;      // levels visited (diagnostic)
 };
 
 constexpr unsigned long long BARRIER_LIMIT_NS = 4000000000ull;  // 4 s
-// Once at most this many vertices remain, block 0 finishes the peel alone
-// with block-level barriers (the remaining levels mostly have tiny rounds).
-constexpr unsigned PEEL_TAIL = 1u << 12;
-
-// Level-synchronous peel of the remaining vertices L[0..len) by one block.
-__device__ void peel_tail(const int64_t *__restrict__ rp, const uint32_t *__restrict__ col, uint32_t *deg,
-                          uint32_t *rnd, uint32_t *core, uint32_t *cur, uint32_t *nxt, uint32_t *L,
-                          uint32_t *L2, unsigned len, unsigned k, unsigned round, PeelState *st)
-{
-    __shared__ unsigned s_len, s_min, s_f;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-    unsigned levels = 0;
-    for (;;) {
-        // drop removed vertices from the list; smallest residual degree
-        if (threadIdx.x == 0) { s_len = 0; s_min = NOT_REMOVED; }
-        __syncthreads();
-        for (unsigned i = threadIdx.x; i < len; i += blockDim.x) {
-            const uint32_t v = L[i];
-            if (rnd[v] == NOT_REMOVED) {
-                L2[atomicAdd(&s_len, 1u)] = v;
-                atomicMin(&s_min, deg[v]);
-            }
-        }
-        __syncthreads();
-        len = s_len;
-        const unsigned md = s_min;
-        { uint32_t *t = L; L = L2; L2 = t; }
-        if (len == 0) break;
-        k = max(k, md);
-        ++levels;
-        if (threadIdx.x == 0) s_f = 0;
-        __syncthreads();
-        for (unsigned i = threadIdx.x; i < len; i += blockDim.x) {
-            const uint32_t v = L[i];
-            if (deg[v] <= k) {
-                rnd[v] = round;
-                core[v] = k;
-                cur[atomicAdd(&s_f, 1u)] = v;
-            }
-        }
-        __syncthreads();
-        unsigned fsize = s_f;
-        while (fsize) {
-            __syncthreads();
-            if (threadIdx.x == 0) s_f = 0;
-            __syncthreads();
-            for (unsigned i = warp; i < fsize; i += nwarps) {
-                const uint32_t v = cur[i];
-                for (int64_t j = rp[v] + lane; j < rp[v + 1]; j += 32) {
-                    const uint32_t u = col[j];
-                    if (rnd[u] == NOT_REMOVED) {
-                        const unsigned old = atomicSub(&deg[u], 1u);
-                        if (old == k + 1) {
-                            rnd[u] = round + 1;
-                            core[u] = k;
-                            nxt[atomicAdd(&s_f, 1u)] = u;
-                        }
-                    }
-                }
-            }
-            __syncthreads();
-            fsize = s_f;
-            ++round;
-            uint32_t *t = cur; cur = nxt; nxt = t;
-        }
-    }
-    if (threadIdx.x == 0) {
-        st->rounds = round;
-        st->levels += levels;
-    }
-}
+constexpr unsigned long long CASCADE_LIMIT_NS = 4000000000ull;  // 4 s without progress
+constexpr uint32_t EMPTY = 0xFFFFFFFFu;
 
 // Grid-wide barrier for a cooperative launch, with a bounded wait: on
 // timeout it sets DERR_TIMEOUT and every block leaves the kernel.
@@ -156,6 +89,7 @@ __device__ bool grid_barrier(PeelState *st, unsigned *err)
         unsigned arrived = atomicAdd(&st->bar_count, 1u) + 1u;
         if (arrived == gridDim.x) {
             st->bar_count = 0;
+            st->rounds++;
             __threadfence();
             atomicAdd(&st->bar_gen, 1u);
         } else {
@@ -181,31 +115,40 @@ __device__ bool grid_barrier(PeelState *st, unsigned *err)
     return s_ok != 0;
 }
 
+// k-core peeling, exact by level, asynchronous within a level.
+//
+// Level k starts when every remaining vertex has residual degree >= k (k is
+// the smallest residual degree).  All remaining vertices of degree <= k are
+// pushed onto one global removal queue; warps then take queue entries one at
+// a time and lower the residual degrees of their neighbours that are still
+// present; a neighbour whose degree falls to k is pushed at once.  The level
+// ends when nothing pushed is left unprocessed.  Every vertex is pushed
+// exactly once, so its queue position is a unique removal time: rnd[v].
+// Out-degree bound: a neighbour pushed after v never lowered deg[v] (v was
+// already removed when it was processed), so at v's push deg[v] <= k counts
+// all of v's later neighbours.
 __global__ void __launch_bounds__(1024) k_peel(int64_t n, const int64_t *__restrict__ rp,
-                                              const uint32_t *__restrict__ col, uint32_t *deg,
-                                              uint32_t *rnd, uint32_t *core, uint32_t *fa,
-                                              uint32_t *fb, uint32_t *tl, PeelState *st, unsigned *err)
+                                               const uint32_t *__restrict__ col, uint32_t *deg,
+                                               uint32_t *rnd, uint32_t *core, uint32_t *lq, PeelState *st,
+                                               unsigned *err)
 {
     const int lane = threadIdx.x & 31;
     const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
-    const int64_t warp = tid >> 5, nwarps = nthreads >> 5;
     volatile PeelState *vst = st;
 
     for (int64_t v = tid; v < n; v += nthreads) {
         deg[v] = (uint32_t)(rp[v + 1] - rp[v]);
         rnd[v] = NOT_REMOVED;
+        lq[v] = EMPTY;
     }
+    if (tid == 0) { st->min_deg[0] = NOT_REMOVED; st->remain[0] = 0; }
     if (!grid_barrier(st, err)) return;
 
-    unsigned k = 0, round = 0, level = 0;
-    uint32_t *cur = fa, *nxt = fb;
-    if (tid == 0) { st->min_deg[0] = NOT_REMOVED; st->remain[0] = 0; st->tlen = 0; }
-    if (!grid_barrier(st, err)) return;
+    unsigned k = 0, level = 0;
+    unsigned claim = EMPTY;  // lane 0: this warp's claimed queue position, kept across levels
     for (;;) {
-        // ---- level start: smallest residual degree among remaining vertices.
-        // The counters of this level (parity) were reset during the previous
-        // level, after everyone had read them two levels ago.
+        // ---- level start: smallest residual degree among remaining vertices
         const unsigned lp = level & 1u;
         {
             unsigned mine = NOT_REMOVED, cntr = 0;
@@ -218,62 +161,84 @@ __global__ void __launch_bounds__(1024) k_peel(int64_t n, const int64_t *__restr
             if (lane == 0 && mine != NOT_REMOVED) { atomicMin(&st->min_deg[lp], mine); atomicAdd(&st->remain[lp], cntr); }
         }
         if (!grid_barrier(st, err)) return;
-        unsigned md = vst->min_deg[lp];
+        const unsigned md = vst->min_deg[lp];
         if (md == NOT_REMOVED) break;  // every vertex removed
-        if (vst->remain[lp] <= PEEL_TAIL) {
-            // hand the last vertices to block 0: no grid barrier after this point
-            for (int64_t v = tid; v < n; v += nthreads)
-                if (rnd[v] == NOT_REMOVED) tl[atomicAdd(&st->tlen, 1u)] = (uint32_t)v;
-            if (!grid_barrier(st, err)) return;
-            if (blockIdx.x == 0)
-                peel_tail(rp, col, deg, rnd, core, cur, nxt, tl, tl + PEEL_TAIL, vst->tlen, k, round, st);
-            return;
-        }
         k = max(k, md);
         if (tid == 0) {
-            // next level's counters (last read before the previous barrier);
-            // cnt[round % 3] is already 0: the previous level ended on it
             st->levels++;
-            st->min_deg[lp ^ 1u] = NOT_REMOVED;
+            st->min_deg[lp ^ 1u] = NOT_REMOVED;  // next level's counters (last read before the barrier above)
             st->remain[lp ^ 1u] = 0;
         }
         ++level;
-        // ---- this level's first frontier: all remaining with deg <= k
-        for (int64_t v = tid; v < n; v += nthreads) {
-            if (rnd[v] == NOT_REMOVED && deg[v] <= k) {
-                rnd[v] = round;
+        // ---- push every remaining vertex of degree <= k (warp-aggregated)
+        for (int64_t base = tid - lane; base < n; base += nthreads) {
+            const int64_t v = base + lane;
+            const bool take = v < n && rnd[v] == NOT_REMOVED && deg[v] <= k;
+            const unsigned b = __ballot_sync(FULL, take);
+            if (!b) continue;
+            unsigned at = 0;
+            if (lane == 0) {
+                at = atomicAdd(&st->tail, (unsigned)__popc(b));
+                atomicAdd(&st->pending, (unsigned)__popc(b));
+            }
+            at = __shfl_sync(FULL, at, 0);
+            if (take) {
+                const unsigned i = at + __popc(b & ((1u << lane) - 1u));
+                rnd[v] = i;
                 core[v] = k;
-                cur[atomicAdd(&st->cnt[round % 3], 1u)] = (uint32_t)v;
+                lq[i] = (uint32_t)v;
             }
         }
         if (!grid_barrier(st, err)) return;
-        // ---- rounds of this level
+        // ---- cascade: take queue entries until nothing is pending
         for (;;) {
-            unsigned fsize = vst->cnt[round % 3];
-            if (fsize == 0) break;
-            if (tid == 0) st->cnt[(round + 2) % 3] = 0;  // free since last round
-            // relax: neighbours reaching k join round+1 (marked on entry)
-            for (int64_t i = warp; i < fsize; i += nwarps) {
-                uint32_t v = cur[i];
-                for (int64_t j = rp[v] + lane; j < rp[v + 1]; j += 32) {
-                    uint32_t u = col[j];
-                    if (rnd[u] == NOT_REMOVED) {
-                        unsigned old = atomicSub(&deg[u], 1u);
-                        if (old == k + 1) {
-                            rnd[u] = round + 1;
-                            core[u] = k;
-                            nxt[atomicAdd(&st->cnt[(round + 1) % 3], 1u)] = u;
-                        }
+            int got = 0;  // 1: vertex in `v`, 2: level done, 3: error
+            uint32_t v = 0;
+            if (lane == 0) {
+                if (claim == EMPTY) claim = atomicAdd(&st->head, 1u);
+                unsigned nap = 32, last = 0xFFFFFFFFu;
+                unsigned long long t0 = global_ns();
+                for (;;) {
+                    if (claim < (uint64_t)n) {
+                        const uint32_t x = *(volatile uint32_t *)(lq + claim);
+                        if (x != EMPTY) { v = x; got = 1; break; }
+                    }
+                    const unsigned pend = vst->pending;
+                    if (pend == 0) { got = 2; break; }
+                    if (*(volatile unsigned *)err & DERR_TIMEOUT) { got = 3; break; }
+                    if (pend != last) { last = pend; t0 = global_ns(); }
+                    else if (global_ns() - t0 > CASCADE_LIMIT_NS) { atomicOr(err, DERR_TIMEOUT); got = 3; break; }
+                    __nanosleep(nap);
+                    nap = min(nap * 2u, 1024u);
+                }
+                if (got == 1) claim = EMPTY;
+            }
+            got = __shfl_sync(FULL, got, 0);
+            if (got == 3) return;
+            if (got == 2) break;
+            v = __shfl_sync(FULL, v, 0);
+            for (int64_t j = rp[v] + lane; j < rp[v + 1]; j += 32) {
+                const uint32_t u = col[j];
+                if (rnd[u] == NOT_REMOVED) {
+                    const unsigned old = atomicSub(&deg[u], 1u);
+                    if (old == k + 1) {
+                        atomicAdd(&st->pending, 1u);
+                        const unsigned i = atomicAdd(&st->tail, 1u);
+                        rnd[u] = i;
+                        core[u] = k;
+                        __threadfence();
+                        *(volatile uint32_t *)(lq + i) = u;
                     }
                 }
             }
-            if (!grid_barrier(st, err)) return;
-            ++round;
-            uint32_t *t = cur; cur = nxt; nxt = t;
+            __syncwarp();
+            if (lane == 0) {
+                __threadfence();
+                atomicSub(&st->pending, 1u);
+            }
         }
-        // the empty frontier counter cnt[round % 3] is reset at the next level start
+        if (!grid_barrier(st, err)) return;
     }
-    if (tid == 0) st->rounds = round;
 }
 
 // ------------------------------------------------------------ orientation
@@ -527,16 +492,13 @@ pvt_status orient_build(pvt_dag *g, uint32_t flags, cudaStream_t s)
         if (st != PVT_OK) return st;
     }
 
-    uint32_t *deg = nullptr, *fa = nullptr, *fb = nullptr, *odeg = nullptr;
+    uint32_t *deg = nullptr, *lq = nullptr, *odeg = nullptr;
     unsigned *dhist = nullptr;
     PeelState *pst = nullptr;
     const size_t nb = (size_t)std::max<int64_t>(n, 1) * sizeof(uint32_t);
     PVT_CK(cudaMallocAsync(&deg, nb, s));
-    PVT_CK(cudaMallocAsync(&fa, nb, s));
-    PVT_CK(cudaMallocAsync(&fb, nb, s));
+    PVT_CK(cudaMallocAsync(&lq, nb, s));
     PVT_CK(cudaMallocAsync(&pst, sizeof(PeelState) + sizeof(unsigned), s));
-    uint32_t *tl = nullptr;
-    PVT_CK(cudaMallocAsync(&tl, 2 * (size_t)PEEL_TAIL * sizeof(uint32_t), s));
     PVT_CK(cudaMallocAsync(&g->rnd, nb, s));
     PVT_CK(cudaMallocAsync(&g->core, nb, s));
     PVT_CK(cudaMemsetAsync(pst, 0, sizeof(PeelState) + sizeof(unsigned), s));
@@ -555,7 +517,7 @@ pvt_status orient_build(pvt_dag *g, uint32_t flags, cudaStream_t s)
         const uint32_t *col = g->col;
         uint32_t *rnd = g->rnd, *core = g->core;
         unsigned *err = g->d_err;
-        void *args[] = {&nn, &rp, &col, &deg, &rnd, &core, &fa, &fb, &tl, &pst, &err};
+        void *args[] = {&nn, &rp, &col, &deg, &rnd, &core, &lq, &pst, &err};
         phase_begin(g, 0, s);
         PVT_CK(cudaLaunchCooperativeKernel((void *)k_peel, dim3(g->num_sms * per_sm), dim3(1024), args,
                                            0, s));
@@ -621,10 +583,8 @@ pvt_status orient_build(pvt_dag *g, uint32_t flags, cudaStream_t s)
     for (int c = 0; c < NCLASS; ++c) g->stats.roots[c] = (uint64_t)g->class_cnt[c];
 
     PVT_CK(cudaFreeAsync(deg, s));
-    PVT_CK(cudaFreeAsync(fa, s));
-    PVT_CK(cudaFreeAsync(fb, s));
+    PVT_CK(cudaFreeAsync(lq, s));
     PVT_CK(cudaFreeAsync(pst, s));
-    PVT_CK(cudaFreeAsync(tl, s));
     PVT_CK(cudaFreeAsync(odeg, s));
     PVT_CK(cudaFreeAsync(dhist, s));
     PVT_CK(cudaStreamSynchronize(s));
