@@ -41,6 +41,8 @@ def parse():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serving-queries", type=int, default=300,
+                    help="queries in the serving stream (the full stream is 10000); 0 skips serving")
     return ap.parse_args()
 
 
@@ -131,6 +133,105 @@ def run_reference(args, ws, rank):
            "cpu_baseline": {"value": value, "unit": "edges/s", "cores": cores, "kind": "oracle", "sample": sample},
            "e2e": {"value": value, "unit": "edges/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
+
+
+def serving_stream(q, seed=5):
+    """Query stream: independent ER or Chung-Lu graphs, n log-uniform in
+    [100, 50000], average degree U[5, 60], exponent U[2.0, 2.5]; each asks
+    global all-k or per-edge counts with probability 1/2."""
+    from paper_2001_06784_gb300 import graphgen
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(q):
+        n = int(np.exp(rng.uniform(np.log(100), np.log(50000))))
+        deg = float(rng.uniform(5, 60))
+        kind = "global" if rng.random() < 0.5 else "edge"
+        if rng.random() < 0.5:
+            rp, col = graphgen.generate(n, er_avg_deg=min(deg, n - 1), seed=5_000_000 + i)
+        else:
+            m = max(1, min(int(n * deg / 2), n * (n - 1) // 4))
+            rp, col = graphgen.generate(n, chung_lu=(m, float(rng.uniform(2.0, 2.5))), seed=5_000_000 + i)
+        out.append((rp, col, kind))
+    return out
+
+
+def run_serving(args, dev):
+    """p50/p99 latency of the query server (continuous batching) against one
+    launch sequence per graph, on the same Poisson arrivals."""
+    import threading as th
+    import torch
+    import paper_2001_06784_gb300 as pvt
+    qs = serving_stream(args.serving_queries)
+    edges = sum(len(c) // 2 for _, c, _ in qs)
+
+    def plain_one(rp, col, kind):
+        rpd = torch.from_numpy(rp).to(dev, non_blocking=True)
+        cd = torch.from_numpy(col.view(np.int32)).to(dev, non_blocking=True)
+        dag = pvt.orient(rpd, cd)
+        out = dag.count_global() if kind == "global" else dag.count_local_edge()
+        host = out.cpu()
+        dag.free()
+        return host
+
+    for rp, col, kind in qs[:3]:  # warm-up
+        plain_one(rp, col, kind)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for rp, col, kind in qs:
+        plain_one(rp, col, kind)
+    sat_s = time.perf_counter() - t0
+    sat_qps = len(qs) / sat_s
+    lam = 0.8 * sat_qps
+    arrivals = np.cumsum(np.random.default_rng(55).exponential(1.0 / lam, len(qs)))
+
+    # plain, replayed in real time: one query at a time in arrival order
+    lat_plain = []
+    t0 = time.perf_counter()
+    for (rp, col, kind), ta in zip(qs, arrivals):
+        now = time.perf_counter() - t0
+        if now < ta:
+            time.sleep(ta - now)
+        plain_one(rp, col, kind)
+        lat_plain.append(time.perf_counter() - t0 - ta)
+    plain_span = time.perf_counter() - t0
+
+    # batched server: a submitter thread keeps the arrivals, latency is
+    # measured inside the server (submit -> result ready)
+    lat_srv = [None] * len(qs)
+    with pvt.Server(mem_budget=64 << 30, max_inflight=4096, max_batch=256, streams=4) as sv:
+        for rp, col, kind in qs[:3]:  # warm-up
+            t = sv.submit(rp, col, kind)
+            sv.wait(t)
+            sv.result(t)
+        tickets = [None] * len(qs)
+        t0 = time.perf_counter()
+
+        def submitter():
+            for i, ((rp, col, kind), ta) in enumerate(zip(qs, arrivals)):
+                now = time.perf_counter() - t0
+                if now < ta:
+                    time.sleep(ta - now)
+                tickets[i] = sv.submit(rp, col, kind)
+
+        thr = th.Thread(target=submitter)
+        thr.start()
+        for i in range(len(qs)):
+            while tickets[i] is None:
+                time.sleep(0.0005)
+            sv.wait(tickets[i])
+            _, lat_srv[i] = sv.result(tickets[i])
+        thr.join()
+        srv_span = time.perf_counter() - t0
+
+    def summary(lat, span):
+        a = np.asarray(lat) * 1000.0
+        return {"p50_ms": float(np.percentile(a, 50)), "p99_ms": float(np.percentile(a, 99)),
+                "mean_ms": float(a.mean()), "throughput_qps": len(a) / span, "edges_per_s": edges / span}
+
+    return {"queries": len(qs), "stream": "ER or Chung-Lu, n log-uniform 100..50000, avg deg U[5,60], "
+                                          "global or per-edge (1/2 each), Poisson arrivals, seed 5",
+            "saturation_qps_plain": sat_qps, "arrival_rate_qps": lam, "edges_total": edges,
+            "plain": summary(lat_plain, plain_span), "batched": summary(lat_srv, srv_span)}
 
 
 def main():
@@ -283,6 +384,10 @@ def main():
            "sct": {"nodes": walk["sct_nodes"], "leaves": walk["sct_leaves"], "pivot_words": walk["pivot_words"],
                    "roots_per_class": walk["roots"], "pivot_words_per_class": walk["class_words"]},
            "peel": {"rounds": so["peel_rounds"], "levels": so["peel_levels"]}}
+
+    # ---- serving: Poisson stream of independent queries (rank 0 only)
+    if rank == 0 and args.serving_queries > 0:
+        out["serving"] = run_serving(args, dev)
 
     # ---- CPU baseline: the oracle, whole workload, every host core; also
     # confirms this run's counts bit-exactly

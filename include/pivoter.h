@@ -58,6 +58,9 @@ typedef struct pvt_dag pvt_dag;
  * Orient the graph along a degeneracy order (Lemma degen, Sec. 3.2; Alg. 1
  * step 1): k-core peeling on the device, then the out-neighbourhoods N+(v)
  * as a CSR over the DAG, every out-degree at most the degeneracy alpha.
+ * alpha_out and pvt_dag_info report alpha = the degeneracy (the top core
+ * level), which bounds every out-degree and does not depend on how removals
+ * within a level are ordered.
  *   n, nnz       vertex count (< 2^32) and row_ptr[n] (= 2m), host values
  *   row_ptr,col  device CSR as above.  It is borrowed, not copied: it must
  *                stay valid and unchanged until pvt_dag_free (per-edge counts
@@ -191,6 +194,59 @@ pvt_status pvt_dag_set_policy(pvt_dag *dag, const pvt_policy *policy);
  */
 pvt_status pvt_count_global_noalloc(int64_t n, const int64_t *orow, const uint32_t *ocol, int32_t alpha,
                                     int32_t kmax, int32_t W, uint64_t *C, void *stream);
+
+/*
+ * Serving: a query server with continuous batching (no counterpart in the
+ * paper; its parallel variant gives whole roots to threads, Sec. 4, and the
+ * root subproblems of many graphs are just as independent).  Queries arrive
+ * with host CSRs; a worker admits them while device memory (mem_budget
+ * bytes, estimated from the CSR and the bound alpha <= sqrt(2m)) and slots
+ * (max_inflight) allow, orients every newly admitted group in one batched
+ * launch (one block per graph), and walks the roots of the whole group in
+ * shared persistent launches; a later group is admitted and oriented while
+ * earlier groups still run, and groups run on separate streams so their work
+ * overlaps.  Results are exact and equal to the single-graph entry points.
+ */
+typedef struct pvt_server pvt_server;
+
+typedef struct pvt_server_config {
+    size_t mem_budget;     /* device bytes for requests in flight (0: 8 GiB) */
+    int32_t max_inflight;  /* requests admitted at once (0: 1024) */
+    int32_t max_batch;     /* graphs per batched launch (0: 256) */
+    int32_t streams;       /* concurrent batches (0: 4) */
+} pvt_server_config;
+
+enum { PVT_QUERY_GLOBAL = 0, PVT_QUERY_VERTEX = 1, PVT_QUERY_EDGE = 2 };
+
+/* Start a server on the current device. */
+pvt_status pvt_server_create(const pvt_server_config *cfg, pvt_server **out);
+
+/*
+ * Submit one query: host CSR (as for pvt_orient; copied before return, so the
+ * caller may reuse its buffers), kind PVT_QUERY_*, kmax < 0 for every k
+ * (alpha + 1).  n must be below 2^32 and the graph's degeneracy at most 512.
+ * ticket receives the query's handle.  Errors: PVT_EINVAL, PVT_ENOMEM (the
+ * query can never fit in mem_budget).
+ */
+pvt_status pvt_server_submit(pvt_server *sv, int64_t n, int64_t nnz, const int64_t *row_ptr,
+                             const uint32_t *col, int32_t kind, int32_t kmax, uint64_t *ticket);
+
+/* Wait up to timeout_ms (< 0: no limit) for a query; *done = 1 when its
+ * result is ready (or it failed: pvt_server_result reports the status). */
+pvt_status pvt_server_wait(pvt_server *sv, uint64_t ticket, int32_t timeout_ms, int32_t *done);
+
+/*
+ * Result of a finished query: rows (1 global, n per-vertex, m per-edge), K
+ * (= kmax + 1) and W as in pvt_count_*; with out != NULL and out_words >=
+ * rows*K*W the words are copied to out (host, layout as pvt_count_*), the
+ * query is released and *latency_s (may be NULL) receives submit-to-done
+ * seconds.  With out == NULL only the sizes are reported.
+ */
+pvt_status pvt_server_result(pvt_server *sv, uint64_t ticket, int64_t *rows, int32_t *K, int32_t *W,
+                             uint64_t *out, size_t out_words, double *latency_s);
+
+/* Stop the server after the queries in flight finish; frees everything. */
+void pvt_server_destroy(pvt_server *sv);
 
 /* Release a pvt_dag and all its device memory (NULL is ignored). */
 void pvt_dag_free(pvt_dag *dag);

@@ -21,7 +21,7 @@ import torch
 from . import _lib
 from ._lib import PVT_PROFILE, PVT_VALIDATE, PivoterError
 
-__all__ = ["orient", "Dag", "to_ints", "count_global_host", "PivoterError"]
+__all__ = ["orient", "Dag", "Server", "to_ints", "count_global_host", "PivoterError"]
 
 
 def _stream_handle(stream, device):
@@ -139,6 +139,67 @@ def orient(row_ptr: torch.Tensor, col: torch.Tensor, *, validate: bool = False, 
                                          _stream_handle(stream, row_ptr.device), ctypes.byref(h),
                                          ctypes.byref(alpha)))
     return Dag(h, row_ptr, col)
+
+
+class Server:
+    """Clique-count query server with continuous batching (pvt_server_*).
+
+    submit() takes a host CSR (numpy) and a query kind ("global", "vertex"
+    or "edge"); queries are admitted by device memory and slots, oriented and
+    walked in shared batched launches; result() returns the words as a numpy
+    uint64 array [rows, K, W] (rows = 1 for global) and the latency."""
+
+    KINDS = {"global": _lib.QUERY_GLOBAL, "vertex": _lib.QUERY_VERTEX, "edge": _lib.QUERY_EDGE}
+
+    def __init__(self, mem_budget: int = 8 << 30, max_inflight: int = 1024, max_batch: int = 256,
+                 streams: int = 4):
+        cfg = _lib.ServerConfig(int(mem_budget), int(max_inflight), int(max_batch), int(streams))
+        h = ctypes.c_void_p()
+        _lib.check(_lib.lib().pvt_server_create(ctypes.byref(cfg), ctypes.byref(h)))
+        self._h = h
+
+    def submit(self, row_ptr, col, kind: str = "global", kmax=None) -> int:
+        rp = np.ascontiguousarray(row_ptr, dtype=np.int64)
+        cl = np.ascontiguousarray(col, dtype=np.uint32)
+        t = ctypes.c_uint64()
+        _lib.check(_lib.lib().pvt_server_submit(self._h, len(rp) - 1, len(cl), rp.ctypes.data,
+                                                cl.ctypes.data if len(cl) else None, self.KINDS[kind],
+                                                -1 if kmax is None else int(kmax), ctypes.byref(t)))
+        return t.value
+
+    def wait(self, ticket: int, timeout_ms: int = -1) -> bool:
+        done = ctypes.c_int32()
+        _lib.check(_lib.lib().pvt_server_wait(self._h, ticket, int(timeout_ms), ctypes.byref(done)))
+        return bool(done.value)
+
+    def result(self, ticket: int):
+        """(words uint64[rows, K, W], latency seconds); releases the query."""
+        rows, K, W = ctypes.c_int64(), ctypes.c_int32(), ctypes.c_int32()
+        _lib.check(_lib.lib().pvt_server_result(self._h, ticket, ctypes.byref(rows), ctypes.byref(K),
+                                                ctypes.byref(W), None, 0, None))
+        out = np.empty((max(rows.value, 0), K.value, W.value), dtype=np.uint64)
+        lat = ctypes.c_double()
+        _lib.check(_lib.lib().pvt_server_result(self._h, ticket, None, None, None,
+                                                out.ctypes.data if out.size else None, out.size,
+                                                ctypes.byref(lat)))
+        return out, lat.value
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.lib().pvt_server_destroy(self._h)
+            self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def to_ints(t):

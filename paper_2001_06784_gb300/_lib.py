@@ -31,10 +31,19 @@ class Policy(ctypes.Structure):
     _fields_ = [("persistent", ctypes.c_int32), ("chunk", ctypes.c_int32)]
 
 
+class ServerConfig(ctypes.Structure):
+    """pvt_server_config (include/pivoter.h)."""
+    _fields_ = [("mem_budget", ctypes.c_size_t), ("max_inflight", ctypes.c_int32),
+                ("max_batch", ctypes.c_int32), ("streams", ctypes.c_int32)]
+
+
+QUERY_GLOBAL, QUERY_VERTEX, QUERY_EDGE = 0, 1, 2
+
 # every symbol include/pivoter.h declares
 EXPORTS = ("pvt_orient", "pvt_dag_info", "pvt_count_global", "pvt_count_local_vertex",
            "pvt_count_local_edge", "pvt_dag_stats", "pvt_dag_set_profiling", "pvt_dag_set_policy",
-           "pvt_count_global_noalloc", "pvt_dag_free",
+           "pvt_count_global_noalloc", "pvt_server_create", "pvt_server_submit", "pvt_server_wait",
+           "pvt_server_result", "pvt_server_destroy", "pvt_dag_free",
            "pvt_last_error")
 
 
@@ -66,6 +75,17 @@ def load(path: str = LIB_PATH):
     lib.pvt_dag_set_policy.argtypes = [vp, ctypes.POINTER(Policy)]
     lib.pvt_count_global_noalloc.restype = i32
     lib.pvt_count_global_noalloc.argtypes = [i64, vp, vp, i32, i32, i32, vp, vp]
+    lib.pvt_server_create.restype = i32
+    lib.pvt_server_create.argtypes = [ctypes.POINTER(ServerConfig), ctypes.POINTER(vp)]
+    lib.pvt_server_submit.restype = i32
+    lib.pvt_server_submit.argtypes = [vp, i64, i64, vp, vp, i32, i32, ctypes.POINTER(ctypes.c_uint64)]
+    lib.pvt_server_wait.restype = i32
+    lib.pvt_server_wait.argtypes = [vp, ctypes.c_uint64, i32, ctypes.POINTER(i32)]
+    lib.pvt_server_result.restype = i32
+    lib.pvt_server_result.argtypes = [vp, ctypes.c_uint64, ctypes.POINTER(i64), ctypes.POINTER(i32),
+                                      ctypes.POINTER(i32), vp, ctypes.c_size_t, ctypes.POINTER(ctypes.c_double)]
+    lib.pvt_server_destroy.restype = None
+    lib.pvt_server_destroy.argtypes = [vp]
     lib.pvt_dag_free.restype = None
     lib.pvt_dag_free.argtypes = [vp]
     lib.pvt_last_error.restype = ctypes.c_char_p

@@ -110,6 +110,7 @@ struct CountArgs {
     int hstride;
     unsigned long long *out;    // local modes: [count][K][W]
     const unsigned long long *B;  // multi-word Pascal table
+    int Bw;                       // words per table entry (>= W)
     int W;
     int kmax;
     unsigned *err;
@@ -229,7 +230,7 @@ __device__ __forceinline__ void add_binom_row(unsigned long long *cell, int s, i
     for (int i = 0; i <= a; ++i) {
         int k = s + i;
         if (k > A.kmax) break;
-        atomic_add_multi(cell + (size_t)k * A.W, binom_at(A.B, a, i, A.W), A.W, A.err);
+        atomic_add_multi(cell + (size_t)k * A.W, binom_at(A.B, a, i, A.Bw), A.W, A.err);
     }
 }
 
@@ -1103,6 +1104,7 @@ pvt_status count_global(pvt_dag *g, int32_t kmax, int32_t W, uint64_t *C, cudaSt
     A.hist = g->hist.p;
     A.hstride = hstride;
     A.B = g->binom.p;
+    A.Bw = W;
     A.W = W;
     A.kmax = kmax;
     A.err = g->d_err;
@@ -1145,6 +1147,7 @@ pvt_status count_local(pvt_dag *g, int32_t kmax, int32_t W, uint64_t *out, bool 
     A.oeid = g->oeid;
     A.out = o;
     A.B = g->binom.p;
+    A.Bw = W;
     A.W = W;
     A.kmax = kmax;
     A.err = g->d_err;
@@ -1154,6 +1157,213 @@ pvt_status count_local(pvt_dag *g, int32_t kmax, int32_t W, uint64_t *out, bool 
     return end_call(g, s, fn);
 }
 
+
+}  // namespace pvt
+
+namespace pvt {
+
+// ----------------------------------------------------------- batched form
+//
+// Roots of many graphs (a served batch) in one persistent launch per
+// (query kind, out-degree class): entry = (graph << 32) | root; each warp
+// reads the graph's descriptor and walks the root exactly as the
+// single-graph kernels do.  Leaf tallies go to the graph's own histogram or
+// table with global atomics.
+
+template <int NW, int MODE>
+__global__ void __launch_bounds__(32 * warps_per_block<NW>())
+    k_count_batch(const BatchGraph *gs, const uint64_t *entries, unsigned nentries, unsigned *qhead,
+                  const unsigned long long *B, int Bw, unsigned *err, unsigned long long *stats)
+{
+    constexpr int WPB = warps_per_block<NW>();
+    extern __shared__ __align__(16) unsigned char smem[];
+    WarpWork<NW> *ww = reinterpret_cast<WarpWork<NW> *>(smem);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    WalkCounters wc;
+    for (;;) {
+        unsigned qi = 0;
+        if (lane == 0) qi = atomicAdd(qhead, 1u);
+        qi = __shfl_sync(FULL, qi, 0);
+        if (qi >= nentries) break;
+        const uint64_t e = entries[qi];
+        const BatchGraph &G = gs[e >> 32];
+        CountArgs A{};
+        A.orow = G.orow;
+        A.ocol = G.ocol;
+        A.oeid = G.oeid;
+        A.hist = G.hist;
+        A.hstride = G.hstride;
+        A.out = G.out;
+        A.B = B;
+        A.Bw = Bw;
+        A.W = G.W;
+        A.kmax = G.kmax;
+        A.err = err;
+        A.stats = stats;
+        walk_root<NW, MODE, false, false>(ww[wid], nullptr, A, lane, (uint32_t)e, wc);
+        if (vload(err) & (DERR_STACK | DERR_RANGE)) break;
+    }
+    (void)WPB;
+    if (lane == 0 && wc.nodes) {
+        atomicAdd(&stats[0], wc.nodes);
+        atomicAdd(&stats[1], wc.leaves);
+        atomicAdd(&stats[2], wc.words);
+    }
+}
+
+// Root entries of every graph of a batch, per (query kind, class):
+// dst[mode][class][off[g][class] + i] = (g << 32) | roots[start + i].
+__global__ void k_batch_entries(const BatchGraph *gs, uint64_t *const *dst, const unsigned *off)
+{
+    const int g = blockIdx.y;
+    const BatchGraph &G = gs[g];
+    const unsigned *start = G.info + BI_START, *cnt = G.info + BI_CNT;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < G.n; i += (int64_t)gridDim.x * blockDim.x) {
+        int c = 0;
+        while (c < NCLASS && !(i >= start[c] && i < start[c] + cnt[c])) ++c;
+        if (c == NCLASS) continue;
+        dst[G.mode * NCLASS + c][off[g * NCLASS + c] + (i - start[c])] = ((uint64_t)g << 32) | G.roots[i];
+    }
+}
+
+// Global counts of the batch's global queries: one block per (graph, k).
+__global__ void __launch_bounds__(256) k_combine_batch(const BatchGraph *gs, const int2 *work,
+                                                       const unsigned long long *__restrict__ B, int Bw,
+                                                       unsigned *err)
+{
+    __shared__ unsigned long long red[256][WMAX];
+    const int2 wk = work[blockIdx.x];
+    const BatchGraph &G = gs[wk.x];
+    const int k = wk.y, W = G.W, hstride = G.hstride;
+    const unsigned long long *hist = G.hist;
+    unsigned long long acc[WMAX];
+#pragma unroll
+    for (int w = 0; w < WMAX; ++w) acc[w] = 0;
+    bool ovf = false;
+    const int pmax = hstride - 2;
+    const int hmax = min(k, hstride - 1);
+    const int total = hmax * (pmax + 1);
+    for (int t = threadIdx.x; t < total; t += blockDim.x) {
+        const int h = 1 + t / (pmax + 1), p = t % (pmax + 1);
+        const int i = k - h;
+        if (i < 0 || i > p) continue;
+        const unsigned long long x = hist[(size_t)h * hstride + p];
+        if (!x) continue;
+        const unsigned long long *b = B + ((size_t)p * (p + 1) / 2 + i) * Bw;
+        unsigned long long carry = 0;
+#pragma unroll
+        for (int w = 0; w < WMAX; ++w) {
+            if (w >= W) break;
+            unsigned long long lo = x * b[w], hi = __umul64hi(x, b[w]);
+            unsigned long long s1 = acc[w] + lo;
+            unsigned long long c1 = s1 < lo;
+            unsigned long long s2 = s1 + carry;
+            unsigned long long c2 = s2 < s1;
+            acc[w] = s2;
+            carry = hi + c1 + c2;
+        }
+        if (carry) ovf = true;
+    }
+#pragma unroll
+    for (int w = 0; w < WMAX; ++w) red[threadIdx.x][w] = acc[w];
+    __syncthreads();
+    for (int stride = 128; stride > 0; stride >>= 1) {
+        if (threadIdx.x < stride) {
+            unsigned long long c = 0;
+            for (int w = 0; w < W; ++w) {
+                unsigned long long x = red[threadIdx.x][w], y = red[threadIdx.x + stride][w];
+                unsigned long long s1 = x + y, c1 = s1 < x, s2 = s1 + c;
+                c = c1 + (s2 < s1);
+                red[threadIdx.x][w] = s2;
+            }
+            if (c) ovf = true;
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x < W) G.out[(size_t)k * W + threadIdx.x] = red[0][threadIdx.x];
+    if (ovf) atomicOr(err, DERR_OVERFLOW);
+}
+
+pvt_status batch_root_entries(BatchGraph *d_graphs, int count, uint64_t *const *d_entries,
+                              const unsigned *d_class_offsets, cudaStream_t s)
+{
+    if (count <= 0) return PVT_OK;
+    k_batch_entries<<<dim3(8, count), 256, 0, s>>>(d_graphs, d_entries, d_class_offsets);
+    PVT_CK(cudaGetLastError());
+    return PVT_OK;
+}
+
+template <int NW, int MODE>
+static pvt_status launch_batch_class(const BatchGraph *gs, const uint64_t *entries, unsigned cnt, unsigned *qhead,
+                                     const unsigned long long *B, int Bw, unsigned *err,
+                                     unsigned long long *stats, int num_sms, cudaStream_t s)
+{
+    constexpr size_t smem = sizeof(WarpWork<NW>) * warps_per_block<NW>();
+    auto kern = k_count_batch<NW, MODE>;
+    PVT_CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    PVT_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * warps_per_block<NW>(), smem));
+    if (per_sm < 1) {
+        set_error("batched walk kernel cannot be resident");
+        return PVT_ECUDA;
+    }
+    const unsigned need = (cnt + warps_per_block<NW>() - 1) / warps_per_block<NW>();
+    const unsigned grid = std::max(1u, std::min<unsigned>((unsigned)(num_sms * per_sm), need));
+    kern<<<grid, 32 * warps_per_block<NW>(), smem, s>>>(gs, entries, cnt, qhead, B, Bw, err, stats);
+    PVT_CK(cudaGetLastError());
+    return PVT_OK;
+}
+
+template <int MODE>
+static pvt_status launch_batch_mode(const BatchGraph *gs, const uint64_t *const *h_entries, const unsigned *n_entries,
+                                    const unsigned long long *B, int Bw, unsigned *ctl, int num_sms, cudaStream_t s)
+{
+    pvt_status st = PVT_OK;
+    for (int c = NCLASS - 1; c >= 0 && st == PVT_OK; --c) {
+        const unsigned cnt = n_entries[MODE * NCLASS + c];
+        if (!cnt) continue;
+        const uint64_t *e = h_entries[MODE * NCLASS + c];
+        unsigned *qhead = ctl + 1 + MODE * NCLASS + c;
+        unsigned *err = ctl;
+        unsigned long long *stats = reinterpret_cast<unsigned long long *>(ctl + 32);
+        switch (c) {
+            case 0:
+            case 1: st = launch_batch_class<1, MODE>(gs, e, cnt, qhead, B, Bw, err, stats, num_sms, s); break;
+            case 2: st = launch_batch_class<2, MODE>(gs, e, cnt, qhead, B, Bw, err, stats, num_sms, s); break;
+            case 3: st = launch_batch_class<4, MODE>(gs, e, cnt, qhead, B, Bw, err, stats, num_sms, s); break;
+            case 4: st = launch_batch_class<8, MODE>(gs, e, cnt, qhead, B, Bw, err, stats, num_sms, s); break;
+            case 5: st = launch_batch_class<16, MODE>(gs, e, cnt, qhead, B, Bw, err, stats, num_sms, s); break;
+        }
+    }
+    return st;
+}
+
+// ctl (device): [0] status word, [1 + mode*NCLASS + class] queue heads,
+// [32..] 64-bit walk statistics; zeroed by the caller.
+pvt_status batch_count(BatchGraph *d_graphs, int count, const int2 *d_combine_work, int n_combine,
+                       const uint64_t *const *h_entries, const unsigned *n_entries,
+                       const unsigned long long *d_binom, int binom_stride, int num_sms, unsigned *d_ctl,
+                       cudaStream_t s)
+{
+    if (count <= 0) return PVT_OK;
+    pvt_status st;
+    if ((st = launch_batch_mode<MODE_GLOBAL>(d_graphs, h_entries, n_entries, d_binom, binom_stride, d_ctl, num_sms, s)) != PVT_OK) return st;
+    if ((st = launch_batch_mode<MODE_VERTEX>(d_graphs, h_entries, n_entries, d_binom, binom_stride, d_ctl, num_sms, s)) != PVT_OK) return st;
+    if ((st = launch_batch_mode<MODE_EDGE>(d_graphs, h_entries, n_entries, d_binom, binom_stride, d_ctl, num_sms, s)) != PVT_OK) return st;
+    if (n_combine > 0) {
+        k_combine_batch<<<n_combine, 256, 0, s>>>(d_graphs, d_combine_work, d_binom, binom_stride, d_ctl);
+        PVT_CK(cudaGetLastError());
+    }
+    return PVT_OK;
+}
+
+// Multi-word Pascal table into caller memory (rows x rows/2 entries of W words).
+pvt_status build_binom(unsigned long long *B, int rows, int W, unsigned *err, cudaStream_t s)
+{
+    k_binom<<<1, 1024, 0, s>>>(B, rows, W, err);
+    PVT_CK(cudaGetLastError());
+    return PVT_OK;
+}
 
 // ------------------------------------------- allocation-free global count
 //
@@ -1294,6 +1504,7 @@ extern "C" pvt_status pvt_count_global_noalloc(int64_t n, const int64_t *orow, c
         A.hist = hist;
         A.hstride = hstride;
         A.B = binom;
+        A.Bw = W;
         A.W = W;
         A.kmax = kmax;
         A.err = err;

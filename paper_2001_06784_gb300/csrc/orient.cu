@@ -69,6 +69,7 @@ struct PeelState {
     unsigned bar_gen;     // grid barrier generation
     unsigned rounds;      // grid barriers passed (diagnostic)
     unsigned levels;      // levels visited (diagnostic)
+    unsigned top_level;   // degeneracy: the last level k
 };
 
 constexpr unsigned long long BARRIER_LIMIT_NS = 4000000000ull;  // 4 s
@@ -162,7 +163,10 @@ __global__ void __launch_bounds__(1024) k_peel(int64_t n, const int64_t *__restr
         }
         if (!grid_barrier(st, err)) return;
         const unsigned md = vst->min_deg[lp];
-        if (md == NOT_REMOVED) break;  // every vertex removed
+        if (md == NOT_REMOVED) {  // every vertex removed
+            if (tid == 0) st->top_level = k;
+            break;
+        }
         k = max(k, md);
         if (tid == 0) {
             st->levels++;
@@ -542,6 +546,14 @@ pvt_status orient_build(pvt_dag *g, uint32_t flags, cudaStream_t s)
     PVT_CK(cudaStreamSynchronize(s));
     st = check_device(g, s, "pvt_orient: peeling");
     if (st != PVT_OK) return st;
+    // alpha = the degeneracy (top core level): it bounds every out-degree and,
+    // unlike the largest out-degree, does not depend on the removal order
+    // within a level
+    if (alpha > hst.top_level) {
+        set_error("pvt_orient: an out-degree exceeds the degeneracy");
+        return PVT_EINTERNAL;
+    }
+    alpha = hst.top_level;
     g->alpha = (int32_t)alpha;
     g->stats.peel_rounds = hst.rounds;
     g->stats.peel_levels = hst.levels;
@@ -589,6 +601,259 @@ pvt_status orient_build(pvt_dag *g, uint32_t flags, cudaStream_t s)
     PVT_CK(cudaFreeAsync(dhist, s));
     PVT_CK(cudaStreamSynchronize(s));
     return check_device(g, s, "pvt_orient");
+}
+
+
+// ----------------------------------------------------- batched orientation
+//
+// Small graphs of a served batch are oriented one block per graph, in a
+// single launch: the same exact-by-level peel with a removal cascade (here on
+// shared-memory counters), the DAG CSR, per-edge ids when the query needs
+// them, and the roots grouped by class.  Block-level waits are bounded.
+
+// Exclusive prefix sum of in[0..n) into out[0..n] (out[n] = total) by one block.
+__device__ void block_scan_u32_i64(const uint32_t *in, int64_t *out, int64_t n)
+{
+    __shared__ long long s_warp[32];
+    __shared__ long long s_carry;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if (threadIdx.x == 0) s_carry = 0;
+    __syncthreads();
+    for (int64_t base = 0; base < n; base += blockDim.x) {
+        const int64_t i = base + threadIdx.x;
+        const long long x = i < n ? (long long)in[i] : 0;
+        long long inc = x;
+        for (int o = 1; o < 32; o <<= 1) {
+            long long t = __shfl_up_sync(FULL, inc, o);
+            if (lane >= o) inc += t;
+        }
+        if (lane == 31) s_warp[wid] = inc;
+        __syncthreads();
+        if (wid == 0) {
+            long long w = lane < nw ? s_warp[lane] : 0, wi = w;
+            for (int o = 1; o < 32; o <<= 1) {
+                long long t = __shfl_up_sync(FULL, wi, o);
+                if (lane >= o) wi += t;
+            }
+            if (lane < nw) s_warp[lane] = wi - w;
+        }
+        __syncthreads();
+        const long long excl = s_carry + s_warp[wid] + inc - x;
+        if (i < n) out[i] = excl;
+        __syncthreads();
+        if (threadIdx.x == blockDim.x - 1) s_carry = excl + x;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[n] = s_carry;
+    __syncthreads();
+}
+
+constexpr unsigned long long BLOCK_WAIT_LIMIT_NS = 2000000000ull;  // 2 s without progress
+
+__global__ void __launch_bounds__(1024) k_orient_batch(BatchGraph *gs)
+{
+    BatchGraph &G = gs[blockIdx.x];
+    const int64_t n = G.n;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const int64_t *rp = G.rp;
+    const uint32_t *col = G.col;
+    uint32_t *deg = G.deg, *rnd = G.rnd, *lq = G.lq;
+    __shared__ unsigned s_len, s_min, s_head, s_tail, s_pending, s_err, s_alpha;
+    __shared__ unsigned s_hist[MAX_ALPHA + 2];
+    __shared__ unsigned s_cls[NCLASS];
+    if (threadIdx.x == 0) { s_head = 0; s_tail = 0; s_pending = 0; s_err = 0; s_alpha = 0; }
+    for (int64_t v = threadIdx.x; v < n; v += blockDim.x) {
+        deg[v] = (uint32_t)(rp[v + 1] - rp[v]);
+        rnd[v] = NOT_REMOVED;
+        lq[v] = 0xFFFFFFFFu;
+        G.tmp[v] = (uint32_t)v;
+    }
+    __syncthreads();
+
+    // ---- 1. peel: exact levels, removal cascade within a level
+    uint32_t *L = G.tmp, *L2 = G.tmp + n;
+    unsigned len = (unsigned)n, k = 0, claim = 0xFFFFFFFFu;
+    for (;;) {
+        if (threadIdx.x == 0) { s_len = 0; s_min = NOT_REMOVED; }
+        __syncthreads();
+        for (unsigned i = threadIdx.x; i < len; i += blockDim.x) {
+            const uint32_t v = L[i];
+            if (rnd[v] == NOT_REMOVED) {
+                L2[atomicAdd(&s_len, 1u)] = v;
+                atomicMin(&s_min, deg[v]);
+            }
+        }
+        __syncthreads();
+        len = s_len;
+        { uint32_t *t = L; L = L2; L2 = t; }
+        if (len == 0) break;
+        k = max(k, s_min);
+        for (unsigned i = threadIdx.x; i < len; i += blockDim.x) {
+            const uint32_t v = L[i];
+            if (deg[v] <= k) {
+                const unsigned t = atomicAdd(&s_tail, 1u);
+                atomicAdd(&s_pending, 1u);
+                rnd[v] = t;
+                lq[t] = v;
+            }
+        }
+        __syncthreads();
+        for (;;) {
+            int got = 0;  // 1 vertex, 2 level done, 3 error
+            uint32_t v = 0;
+            if (lane == 0) {
+                if (claim == 0xFFFFFFFFu) claim = atomicAdd(&s_head, 1u);
+                unsigned last = 0xFFFFFFFFu;
+                unsigned long long t0 = global_ns();
+                for (;;) {
+                    if (claim < (uint64_t)n) {
+                        const uint32_t x = *(volatile uint32_t *)(lq + claim);
+                        if (x != 0xFFFFFFFFu) { v = x; got = 1; break; }
+                    }
+                    const unsigned pend = *(volatile unsigned *)&s_pending;
+                    if (pend == 0) { got = 2; break; }
+                    if (*(volatile unsigned *)&s_err) { got = 3; break; }
+                    if (pend != last) { last = pend; t0 = global_ns(); }
+                    else if (global_ns() - t0 > BLOCK_WAIT_LIMIT_NS) { atomicOr(&s_err, DERR_TIMEOUT); got = 3; break; }
+                    __nanosleep(32);
+                }
+                if (got == 1) claim = 0xFFFFFFFFu;
+            }
+            got = __shfl_sync(FULL, got, 0);
+            if (got != 1) break;
+            v = __shfl_sync(FULL, v, 0);
+            for (int64_t j = rp[v] + lane; j < rp[v + 1]; j += 32) {
+                const uint32_t u = col[j];
+                if (rnd[u] == NOT_REMOVED) {
+                    const unsigned old = atomicSub(&deg[u], 1u);
+                    if (old == k + 1) {
+                        atomicAdd(&s_pending, 1u);
+                        const unsigned t = atomicAdd(&s_tail, 1u);
+                        rnd[u] = t;
+                        __threadfence_block();
+                        *(volatile uint32_t *)(lq + t) = u;
+                    }
+                }
+            }
+            __syncwarp();
+            if (lane == 0) {
+                __threadfence_block();
+                atomicSub(&s_pending, 1u);
+            }
+        }
+        __syncthreads();
+        if (s_err) break;
+    }
+    __syncthreads();
+    if (s_err) {
+        if (threadIdx.x == 0) G.info[BI_ERR] = s_err;
+        return;
+    }
+    const unsigned top_level = k;  // degeneracy
+
+    // ---- 2. DAG: out-degrees (into deg), offsets, out-lists in id order
+    for (int64_t v = wid; v < n; v += nwarps) {
+        const uint32_t rv = rnd[v];
+        unsigned c = 0;
+        for (int64_t j = rp[v] + lane; j < rp[v + 1]; j += 32) c += rnd[col[j]] > rv;
+        for (int o = 16; o; o >>= 1) c += __shfl_xor_sync(FULL, c, o);
+        if (lane == 0) {
+            deg[v] = c;
+            atomicMax(&s_alpha, c);
+        }
+    }
+    __syncthreads();
+    block_scan_u32_i64(deg, G.orow, n);
+    for (int64_t v = wid; v < n; v += nwarps) {
+        const uint32_t rv = rnd[v];
+        int64_t out = G.orow[v];
+        for (int64_t j0 = rp[v]; j0 < rp[v + 1]; j0 += 32) {
+            const int64_t j = j0 + lane;
+            uint32_t u = 0;
+            bool keep = false;
+            if (j < rp[v + 1]) {
+                u = col[j];
+                keep = rnd[u] > rv;
+            }
+            const unsigned b = __ballot_sync(FULL, keep);
+            if (keep) G.ocol[out + __popc(b & ((1u << lane) - 1u))] = u;
+            out += __popc(b);
+        }
+    }
+    __syncthreads();
+
+    // ---- 3. edge ids (rank of (min, max) in lexicographic order)
+    if (G.oeid) {
+        for (int64_t v = threadIdx.x; v < n; v += blockDim.x) {
+            int64_t lo = rp[v], hi = rp[v + 1], e = hi;
+            while (lo < hi) {
+                int64_t mid = lo + ((hi - lo) >> 1);
+                if (col[mid] <= (uint32_t)v) lo = mid + 1; else hi = mid;
+            }
+            L[v] = (uint32_t)(e - lo);  // neighbours above v (tmp is free now)
+        }
+        __syncthreads();
+        block_scan_u32_i64(L, G.up, n);
+        for (int64_t r = wid; r < n; r += nwarps) {
+            for (int64_t j = G.orow[r] + lane; j < G.orow[r + 1]; j += 32) {
+                const uint32_t u = G.ocol[j];
+                const uint32_t a = min((uint32_t)r, u), b = max((uint32_t)r, u);
+                int64_t lo = rp[a], hi = rp[a + 1];
+                while (lo < hi) {
+                    int64_t mid = lo + ((hi - lo) >> 1);
+                    if (col[mid] < b) lo = mid + 1; else hi = mid;
+                }
+                const int64_t pos = lo;
+                lo = rp[a];
+                hi = rp[a + 1];
+                while (lo < hi) {
+                    int64_t mid = lo + ((hi - lo) >> 1);
+                    if (col[mid] <= a) lo = mid + 1; else hi = mid;
+                }
+                G.oeid[j] = (uint32_t)(G.up[a] + (pos - lo));
+            }
+        }
+        __syncthreads();
+    }
+
+    // ---- 4. roots by class, out-degree descending (counting sort)
+    const unsigned alpha = top_level;  // bounds every out-degree (s_alpha)
+    if (s_alpha > top_level || alpha > MAX_ALPHA) {
+        if (threadIdx.x == 0) { G.info[BI_ALPHA] = alpha; G.info[BI_ERR] = DERR_RANGE; }
+        return;
+    }
+    for (unsigned d = threadIdx.x; d <= alpha; d += blockDim.x) s_hist[d] = 0;
+    __syncthreads();
+    for (int64_t v = threadIdx.x; v < n; v += blockDim.x) atomicAdd(&s_hist[deg[v]], 1u);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned pos = 0;
+        for (int c = 0; c < NCLASS; ++c) s_cls[c] = 0;
+        for (int d = (int)alpha; d >= 0; --d) {
+            const unsigned c = s_hist[d];
+            s_hist[d] = pos;
+            pos += c;
+            s_cls[degree_class((uint32_t)d)] += c;
+        }
+        unsigned off = 0;
+        for (int c = NCLASS - 1; c >= 0; --c) {
+            G.info[BI_START + c] = off;
+            G.info[BI_CNT + c] = s_cls[c];
+            off += s_cls[c];
+        }
+        G.info[BI_ALPHA] = alpha;
+        G.info[BI_ERR] = 0;
+    }
+    __syncthreads();
+    for (int64_t v = threadIdx.x; v < n; v += blockDim.x) G.roots[atomicAdd(&s_hist[deg[v]], 1u)] = (uint32_t)v;
+}
+
+pvt_status batch_orient(BatchGraph *d_graphs, int count, cudaStream_t s)
+{
+    if (count <= 0) return PVT_OK;
+    k_orient_batch<<<count, 1024, 0, s>>>(d_graphs);
+    PVT_CK(cudaGetLastError());
+    return PVT_OK;
 }
 
 }  // namespace pvt

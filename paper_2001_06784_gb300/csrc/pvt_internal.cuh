@@ -77,6 +77,45 @@ struct pvt_dag {
 
 namespace pvt {
 
+// One graph of a batched launch: a device-resident descriptor filled by the
+// host, completed by the batched orient kernel (one block per graph).
+enum BatchMode : int { BATCH_GLOBAL = 0, BATCH_VERTEX = 1, BATCH_EDGE = 2 };
+enum BatchInfo : int { BI_ALPHA = 0, BI_ERR = 1, BI_CNT = 2, BI_START = 8 };  // info[] slots
+struct BatchGraph {
+    int64_t n = 0, nnz = 0;
+    const int64_t *rp = nullptr;      // undirected CSR
+    const uint32_t *col = nullptr;
+    uint32_t *deg = nullptr, *rnd = nullptr, *lq = nullptr, *tmp = nullptr;  // scratch: n, n, n, 2n
+    int64_t *orow = nullptr;          // DAG
+    uint32_t *ocol = nullptr;
+    uint32_t *oeid = nullptr;         // per-edge queries only
+    int64_t *up = nullptr;            //   (n+1 scratch for edge ids)
+    uint32_t *roots = nullptr;        // n, grouped by class, out-degree descending
+    uint32_t info[16] = {};           // alpha, status, class counts [2..7], class starts [8..13]
+    unsigned long long *hist = nullptr;  // global queries: (h, p) histogram
+    int hstride = 0;
+    unsigned long long *out = nullptr;   // result: C [K][W], or table [rows][K][W]
+    int mode = BATCH_GLOBAL;
+    int kmax = 0, W = 1;
+};
+
+// Batched orientation: one block per graph (peel, DAG CSR, edge ids for
+// per-edge queries, root classes) for `count` device descriptors.
+pvt_status batch_orient(BatchGraph *d_graphs, int count, cudaStream_t s);
+// Batched walk of the root entries h_entries[mode * NCLASS + class] (device
+// arrays of (graph << 32 | root), n_entries each) and the combine of the
+// global queries (d_combine_work: (graph, k) per block).  d_ctl: zeroed
+// status word, queue heads and statistics (see count.cu).
+pvt_status batch_count(BatchGraph *d_graphs, int count, const int2 *d_combine_work, int n_combine,
+                       const uint64_t *const *h_entries, const unsigned *n_entries,
+                       const unsigned long long *d_binom, int binom_stride, int num_sms, unsigned *d_ctl,
+                       cudaStream_t s);
+// Fill the per-(mode, class) root entry lists of a batch from the descriptors.
+pvt_status batch_root_entries(BatchGraph *d_graphs, int count, uint64_t *const *d_entries,
+                              const unsigned *d_class_offsets /*[count][NCLASS]*/, cudaStream_t s);
+// Multi-word Pascal table C(a, b), a < rows, W words per entry.
+pvt_status build_binom(unsigned long long *B, int rows, int W, unsigned *err, cudaStream_t s);
+
 // Thread-local error message used by pvt_last_error().
 void set_error(const std::string &msg);
 
