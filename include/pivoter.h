@@ -126,18 +126,18 @@ pvt_status pvt_count_local_edge(pvt_dag *dag, int32_t kmax, int32_t W, uint64_t 
  * leaf), root-to-leaf paths, and the bitset words ANDed and popcounted in
  * pivot selection (|S| * ceil(d/32) per internal node).  ms[] holds device
  * time per phase when profiling is on (else zeros): [0] peel, [1] orient
- * (DAG CSR and root classes), [2..6] the walk kernels of out-degree classes
- * <=32, <=64, <=128, <=256, <=512, [7] combine/finish.  Phases of different
- * classes overlap in time.
+ * (DAG CSR and root classes), [2..7] the walk kernels of out-degree classes
+ * <=32, <=64, <=128, <=256, <=512, <=1024, [8] combine/finish.  Phases of
+ * different classes overlap in time.
  */
 typedef struct pvt_stats {
     uint64_t sct_nodes;
     uint64_t sct_leaves;
     uint64_t pivot_words;
     uint64_t launches;      /* kernels launched by the call */
-    uint64_t roots[6];      /* roots per out-degree class (0, <=32, ..., <=512) */
-    uint64_t class_words[6];/* pivot_words split by out-degree class */
-    float ms[8];
+    uint64_t roots[7];      /* roots per out-degree class (0, <=32, ..., <=1024) */
+    uint64_t class_words[7];/* pivot_words split by out-degree class */
+    float ms[9];
     uint32_t peel_rounds;   /* orient: grid-wide barriers of the peel */
     uint32_t peel_levels;   /* orient: distinct core levels visited */
 } pvt_stats;

@@ -84,7 +84,8 @@ class Dag:
                                                    _stream_handle(stream, self.device)))
         return out
 
-    PHASES = ("peel", "orient", "walk_d32", "walk_d64", "walk_d128", "walk_d256", "walk_d512", "finish")
+    PHASES = ("peel", "orient", "walk_d32", "walk_d64", "walk_d128", "walk_d256", "walk_d512", "walk_d1024",
+              "finish")
 
     def stats(self):
         """Statistics of the last call on this dag (see pvt_stats): SCT walk

@@ -23,8 +23,8 @@ class Stats(ctypes.Structure):
     """pvt_stats (include/pivoter.h)."""
     _fields_ = [("sct_nodes", ctypes.c_uint64), ("sct_leaves", ctypes.c_uint64),
                 ("pivot_words", ctypes.c_uint64), ("launches", ctypes.c_uint64),
-                ("roots", ctypes.c_uint64 * 6), ("class_words", ctypes.c_uint64 * 6),
-                ("ms", ctypes.c_float * 8), ("peel_rounds", ctypes.c_uint32), ("peel_levels", ctypes.c_uint32)]
+                ("roots", ctypes.c_uint64 * 7), ("class_words", ctypes.c_uint64 * 7),
+                ("ms", ctypes.c_float * 9), ("peel_rounds", ctypes.c_uint32), ("peel_levels", ctypes.c_uint32)]
 
 class Policy(ctypes.Structure):
     """pvt_policy (include/pivoter.h)."""

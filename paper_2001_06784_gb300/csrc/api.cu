@@ -54,7 +54,7 @@ void phase_end(pvt_dag *g, int ph, cudaStream_t s)
 void stats_reset(pvt_dag *g)
 {
     g->stats = pvt_stats{};
-    for (int i = 0; i < 8; ++i) g->phase_used[i] = false;
+    for (int i = 0; i < NPHASE; ++i) g->phase_used[i] = false;
 }
 
 static void dag_release(pvt_dag *g)
@@ -66,7 +66,7 @@ static void dag_release(pvt_dag *g)
         if (g->ev_join[c]) cudaEventDestroy(g->ev_join[c]);
     }
     if (g->ev_fork) cudaEventDestroy(g->ev_fork);
-    for (int i = 0; i < 8; ++i) {
+    for (int i = 0; i < NPHASE; ++i) {
         if (g->ev_t0[i]) cudaEventDestroy(g->ev_t0[i]);
         if (g->ev_t1[i]) cudaEventDestroy(g->ev_t1[i]);
     }
@@ -87,6 +87,7 @@ static void dag_release(pvt_dag *g)
         cudaFree(g->qready[c].p);
     }
     cudaFree(g->qctl);
+    for (int c = 0; c < NCLASS; ++c) cudaFree(g->gstack[c].p);
     cudaFree(g->d_stats);
     if (g->h_err) cudaFreeHost(g->h_err);
     if (g->h_stats) cudaFreeHost(g->h_stats);
@@ -122,7 +123,7 @@ pvt_status pvt_orient(int64_t n, int64_t nnz, const int64_t *row_ptr, const uint
     if (e == cudaSuccess) e = cudaMalloc(&g->d_q, 16 * sizeof(unsigned));
     if (e == cudaSuccess) e = cudaMalloc(&g->d_stats, 16 * sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaMalloc(&g->qctl, NCLASS * 128 * sizeof(uint32_t));
-    for (int i = 0; i < 8 && e == cudaSuccess; ++i) {
+    for (int i = 0; i < NPHASE && e == cudaSuccess; ++i) {
         e = cudaEventCreate(&g->ev_t0[i]);
         if (e == cudaSuccess) e = cudaEventCreate(&g->ev_t1[i]);
     }
@@ -191,7 +192,7 @@ pvt_status pvt_dag_stats(const pvt_dag *dag, pvt_stats *out)
         return PVT_EINVAL;
     }
     *out = dag->stats;
-    for (int i = 0; i < 8; ++i) {
+    for (int i = 0; i < NPHASE; ++i) {
         out->ms[i] = 0.f;
         if (!dag->phase_used[i]) continue;
         float ms = 0.f;

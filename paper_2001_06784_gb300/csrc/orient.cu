@@ -659,7 +659,7 @@ __global__ void __launch_bounds__(1024) k_orient_batch(BatchGraph *gs)
     const uint32_t *col = G.col;
     uint32_t *deg = G.deg, *rnd = G.rnd, *lq = G.lq;
     __shared__ unsigned s_len, s_min, s_head, s_tail, s_pending, s_err, s_alpha;
-    __shared__ unsigned s_hist[MAX_ALPHA + 2];
+    __shared__ unsigned s_hist[BATCH_MAX_ALPHA + 2];
     __shared__ unsigned s_cls[NCLASS];
     if (threadIdx.x == 0) { s_head = 0; s_tail = 0; s_pending = 0; s_err = 0; s_alpha = 0; }
     for (int64_t v = threadIdx.x; v < n; v += blockDim.x) {
@@ -818,7 +818,7 @@ __global__ void __launch_bounds__(1024) k_orient_batch(BatchGraph *gs)
 
     // ---- 4. roots by class, out-degree descending (counting sort)
     const unsigned alpha = top_level;  // bounds every out-degree (s_alpha)
-    if (s_alpha > top_level || alpha > MAX_ALPHA) {
+    if (s_alpha > top_level || alpha > BATCH_MAX_ALPHA) {
         if (threadIdx.x == 0) { G.info[BI_ALPHA] = alpha; G.info[BI_ERR] = DERR_RANGE; }
         return;
     }

@@ -15,8 +15,10 @@ constexpr uint32_t NOT_REMOVED = 0xFFFFFFFFu;
 
 // Root classes by out-degree d = |N+(r)|: class 0 holds d = 0, class c >= 1
 // holds 32 * 2^(c-2) < d <= 32 * 2^(c-1), i.e. bitsets of NW = 2^(c-1) words.
-constexpr int NCLASS = 6;              // d = 0, <=32, <=64, <=128, <=256, <=512
-constexpr int MAX_ALPHA = 512;         // largest out-degree with shared-memory bitsets
+constexpr int NCLASS = 7;              // d = 0, <=32, <=64, <=128, <=256, <=512, <=1024
+constexpr int MAX_ALPHA = 1024;        // largest degeneracy (out-degree) supported
+constexpr int BATCH_MAX_ALPHA = 512;   // largest degeneracy of a served (batched) graph
+constexpr int NPHASE = NCLASS + 2;     // peel, orient, one walk per class >= 1, finish
 constexpr int WMAX = 20;               // largest W (64-bit words per count) supported
 
 // Device-side error bits (one 32-bit status word per dag).
@@ -71,8 +73,9 @@ struct pvt_dag {
     pvt_stats stats = {};
     bool profiling = false;
     pvt_policy policy = {1, 4};
-    cudaEvent_t ev_t0[8] = {}, ev_t1[8] = {};
-    bool phase_used[8] = {};
+    cudaEvent_t ev_t0[pvt::NPHASE] = {}, ev_t1[pvt::NPHASE] = {};
+    bool phase_used[pvt::NPHASE] = {};
+    pvt::DevBuf<uint32_t> gstack[pvt::NCLASS];  // DFS stacks of the wide classes (global memory)
 };
 
 namespace pvt {
@@ -80,7 +83,7 @@ namespace pvt {
 // One graph of a batched launch: a device-resident descriptor filled by the
 // host, completed by the batched orient kernel (one block per graph).
 enum BatchMode : int { BATCH_GLOBAL = 0, BATCH_VERTEX = 1, BATCH_EDGE = 2 };
-enum BatchInfo : int { BI_ALPHA = 0, BI_ERR = 1, BI_CNT = 2, BI_START = 8 };  // info[] slots
+enum BatchInfo : int { BI_ALPHA = 0, BI_ERR = 1, BI_CNT = 2, BI_START = 9 };  // info[] slots
 struct BatchGraph {
     int64_t n = 0, nnz = 0;
     const int64_t *rp = nullptr;      // undirected CSR
@@ -91,7 +94,7 @@ struct BatchGraph {
     uint32_t *oeid = nullptr;         // per-edge queries only
     int64_t *up = nullptr;            //   (n+1 scratch for edge ids)
     uint32_t *roots = nullptr;        // n, grouped by class, out-degree descending
-    uint32_t info[16] = {};           // alpha, status, class counts [2..7], class starts [8..13]
+    uint32_t info[16] = {};           // alpha, status, class counts [2..8], class starts [9..15]
     unsigned long long *hist = nullptr;  // global queries: (h, p) histogram
     int hstride = 0;
     unsigned long long *out = nullptr;   // result: C [K][W], or table [rows][K][W]

@@ -33,7 +33,7 @@ using Clock = std::chrono::steady_clock;
 enum ReqState { REQ_PENDING, REQ_RUNNING, REQ_DONE, REQ_FAILED };
 
 constexpr size_t ALIGN = 256;
-constexpr int BINOM_ROWS = MAX_ALPHA + 3;  // every degeneracy the kernels accept
+constexpr int BINOM_ROWS = BATCH_MAX_ALPHA + 3;  // every degeneracy a served graph may have
 constexpr int BINOM_W = WMAX;
 
 size_t align_up(size_t x) { return (x + ALIGN - 1) / ALIGN * ALIGN; }
@@ -126,7 +126,7 @@ int alpha_bound(const Request &r)
     int64_t maxdeg = 0;
     for (int64_t v = 0; v < r.n; ++v) maxdeg = std::max<int64_t>(maxdeg, r.rp[v + 1] - r.rp[v]);
     const int64_t sq = (int64_t)std::floor(std::sqrt(2.0 * (double)r.m)) + 1;
-    return (int)std::min<int64_t>(std::min<int64_t>(maxdeg, sq), MAX_ALPHA);
+    return (int)std::min<int64_t>(std::min<int64_t>(maxdeg, sq), BATCH_MAX_ALPHA);
 }
 
 }  // namespace

@@ -1,0 +1,11 @@
+// Walk kernels of the out-degree class with 16-word bitsets (edge counts).
+#include "walk.cuh"
+
+namespace pvt {
+
+template pvt_status launch_class<16, MODE_EDGE, false>(pvt_dag *, const CountArgs &, int, cudaStream_t);
+template pvt_status launch_batch_class<16, MODE_EDGE>(const BatchGraph *, const uint64_t *, unsigned, unsigned *,
+                                                    const unsigned long long *, int, unsigned *, unsigned long long *,
+                                                    int, cudaStream_t);
+
+}  // namespace pvt

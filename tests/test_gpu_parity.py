@@ -107,6 +107,14 @@ def test_wide_branching_random(pvt, n, missing, vertex):
     check_all(pvt, rp, col, vertex=vertex, edge=False)
 
 
+@pytest.mark.parametrize("make", [lambda: graphs.clique_minus_random(520, 4, 3), lambda: graphs.complete(530)])
+def test_widest_class_global(pvt, make):
+    # out-degrees above 512: 32-word bitsets with the DFS stack in global memory
+    rp, col = make()
+    ref = check_all(pvt, rp, col, vertex=False, edge=False)
+    assert ref["alpha"] > 512
+
+
 @pytest.mark.parametrize("kmax", [0, 1, 2, 3, 5, 9])
 def test_truncation(pvt, kmax):
     rp, col = graphgen.generate(400, er_avg_deg=10.0, planted=[(2, 15, 25, 1.0)], seed=3)
