@@ -208,6 +208,43 @@ def run_local(args, dev, flush):
     return res
 
 
+def run_graph_replay(args, dev, reps=50):
+    """Global counts on a resident small graph (ER n=2000, avg degree 20,
+    one 30-clique), called repeatedly: the launch sequence issued directly
+    against the replay of its recorded CUDA graph (device time per call,
+    CUDA events around each call)."""
+    import torch
+    import paper_2001_06784_gb300 as pvt
+    from paper_2001_06784_gb300 import graphgen
+    name = "er2k_d20_clique30"
+    rp, col = graphgen.workload(name)
+    dag = pvt.orient(torch.from_numpy(rp).to(dev), torch.from_numpy(col.view(np.int32)).to(dev))
+    stream = torch.cuda.current_stream(dev)
+    out = torch.empty((dag.alpha + 2, dag.min_words), dtype=torch.int64, device=dev)
+    res = {"workload": name}
+    ref = None
+    for form in ("direct", "graph"):
+        dag.set_policy(graph=(form == "graph"))
+        ms = []
+        for i in range(reps + 3):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            t0 = time.perf_counter()
+            e0.record(stream)
+            dag.count_global(out=out)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            if i >= 3:
+                ms.append((e0.elapsed_time(e1), (time.perf_counter() - t0) * 1000.0))
+        got = pvt.to_ints(out)
+        ref = got if ref is None else ref
+        assert got == ref, "graph replay differs from direct launches"
+        res[form] = {"device_ms": float(np.median([a for a, _ in ms])),
+                     "host_ms": float(np.median([b for _, b in ms])), "launches": dag.stats()["launches"]}
+    dag.free()
+    return res
+
+
 def run_serving(args, dev):
     """p50/p99 latency of the query server (continuous batching) against one
     launch sequence per graph, on the same Poisson arrivals."""
@@ -321,6 +358,13 @@ def main():
         alpha, W = dag.alpha, dag.min_words
         dag.free()
     kmax = alpha + 1
+    # launch policy per out-degree class, picked once by the library's
+    # autotuner and applied to every step's dag
+    dag = pvt.orient(rp_d, col_d)
+    policy, tune_ms, Ct = dag.autotune(kmax=kmax, W=W)
+    tuned_C = pvt.to_ints(Ct)
+    dag.free()
+    step_policy = dict(policy, graph=False)
 
     # ---- device-resident timed steps (L2 flushed between steps)
     sampler = ClockSampler(local)
@@ -336,6 +380,7 @@ def main():
         e0.record(stream)
         dag = pvt.orient(rp_d, col_d, profile=True)
         so = dag.stats()
+        dag.set_policy(**step_policy)
         C = dag.count_global(kmax=kmax, W=W)
         e1.record(stream)
         sc = dag.stats()
@@ -358,6 +403,7 @@ def main():
     value = ws * m * args.steps / total_s
     C_words = C.cpu()
     C_ints = pvt.to_ints(C_words)
+    assert tuned_C == C_ints, "autotuner run and timed steps differ"
     omega = max(k for k, c in enumerate(C_ints) if c)
 
     # ---- the plain form on the same steps: one warp per root, one launch per
@@ -390,6 +436,7 @@ def main():
         rp_x = rp_h.to(dev, non_blocking=True)
         col_x = col_h.to(dev, non_blocking=True)
         dag = pvt.orient(rp_x, col_x)
+        dag.set_policy(**step_policy)
         Cx = dag.count_global(kmax=kmax, W=W)
         C_host.copy_(Cx, non_blocking=True)
         e1.record(stream)
@@ -424,6 +471,9 @@ def main():
            "vs_baseline": None, "dtype": "u64 words (exact integers)", "data": "synthetic",
            "config": {"workload": args.workload, "n": n, "m": m, "alpha": alpha, "omega": omega, "kmax": kmax,
                       "W": W, "form": "persistent work queue", "l2": "flushed (256 MiB write) between steps",
+                      "policy": step_policy,
+                      "autotune_ms": {c: [round(float(x), 3) for x in tune_ms[i]]
+                                      for i, c in enumerate(("chunk4_split", "chunk1_nosplit", "chunk16_split"))},
                       "parallelism": "replicas" if ws > 1 else "single"},
            "roofline": roofline,
            "e2e": {"value": e2e_value, "unit": "edges/s", "ms_per_step": e2e_s * 1000.0 / len(e2e_ms),
@@ -437,6 +487,10 @@ def main():
            "sct": {"nodes": walk["sct_nodes"], "leaves": walk["sct_leaves"], "pivot_words": walk["pivot_words"],
                    "roots_per_class": walk["roots"], "pivot_words_per_class": walk["class_words"]},
            "peel": {"rounds": so["peel_rounds"], "levels": so["peel_levels"]}}
+
+    # ---- launch cost: direct launches vs replay of the recorded CUDA graph
+    if rank == 0:
+        out["graph_replay"] = run_graph_replay(args, dev)
 
     # ---- local counts (per-vertex, per-edge) on the 500k-vertex graph
     if rank == 0 and not args.no_local:

@@ -157,14 +157,47 @@ pvt_status pvt_dag_set_profiling(pvt_dag *dag, int32_t enable);
  *               one launch per class.
  *   chunk       roots taken per queue access in the <=32 class (1..32,
  *               default 4); ignored by the plain form.
+ *   split[c]    per out-degree class c (0, <=32, ..., <=1024): 1 lets the
+ *               warps of a global count share the subtrees of heavy roots
+ *               through a device frame queue (many warps on one root);
+ *               0 keeps one warp per root.  Only classes with out-degree
+ *               above 32 can split, and only in the persistent form; local
+ *               counts never split.  Default {0, 0, 1, 1, 1, 1, 1}.
+ *   graph       1: pvt_count_global records its launch sequence as a CUDA
+ *               graph at the first call with a given (kmax, W, C) and
+ *               replays it at later calls with the same three (the dag's
+ *               buffers are fixed after orientation); 0 (default): launch
+ *               directly.  Replayed calls report no phase times.
+ * Each field is checked: PVT_EINVAL for a value out of range.
  */
 typedef struct pvt_policy {
     int32_t persistent;
     int32_t chunk;
+    int32_t split[7];
+    int32_t graph;
 } pvt_policy;
 
-/* Set the launch policy for later count calls on this dag. */
+/* Set the launch policy for later count calls on this dag (drops a recorded
+ * graph). */
 pvt_status pvt_dag_set_policy(pvt_dag *dag, const pvt_policy *policy);
+
+/* Copy the dag's current launch policy into *out (host). */
+pvt_status pvt_dag_get_policy(const pvt_dag *dag, pvt_policy *out);
+
+/*
+ * Autotuner of the launch policy (no counterpart in the paper).  Runs
+ * pvt_count_global(dag, kmax, W, C, stream) under three candidate policies
+ * -- {chunk 4, split}, {chunk 1, no split}, {chunk 16, split} -- twice each,
+ * with the out-degree classes launched one after another and timed with CUDA
+ * events, then keeps per class the fastest: the chunk of the <=32 class and,
+ * for every wider class, whether its heavy roots split across warps.  The
+ * chosen policy (persistent, graph flag unchanged) is set on the dag and
+ * copied to *chosen; ms (host float[3][7], may be NULL) receives the second
+ * timing of each class under each candidate.  C holds the counts on return;
+ * errors as pvt_count_global.
+ */
+pvt_status pvt_dag_autotune(pvt_dag *dag, int32_t kmax, int32_t W, uint64_t *C, void *stream,
+                            pvt_policy *chosen, float *ms);
 
 /*
  * Global counts without any device allocation.  The paper has no

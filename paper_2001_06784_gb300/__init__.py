@@ -98,11 +98,37 @@ class Dag:
                     ms=dict(zip(self.PHASES, list(st.ms))), peel_rounds=st.peel_rounds,
                     peel_levels=st.peel_levels)
 
-    def set_policy(self, persistent: bool = True, chunk: int = 4):
+    def policy(self):
+        """The dag's launch policy (pvt_policy) as a dict."""
+        pol = _lib.Policy()
+        _lib.check(_lib.lib().pvt_dag_get_policy(self._h, ctypes.byref(pol)))
+        return dict(persistent=bool(pol.persistent), chunk=pol.chunk, split=list(pol.split), graph=bool(pol.graph))
+
+    def set_policy(self, persistent: bool = True, chunk: int = 4, split=None, graph: bool = False):
         """Launch policy of the walk kernels: persistent warps with a device
-        work queue (default) or the plain one-warp-per-root form."""
-        pol = _lib.Policy(1 if persistent else 0, int(chunk))
+        work queue (default) or the plain one-warp-per-root form; per
+        out-degree class whether heavy roots split across warps (7 flags,
+        default: every class above out-degree 32); and whether global counts
+        replay a recorded CUDA graph."""
+        split = [0, 0, 1, 1, 1, 1, 1] if split is None else [int(x) for x in split]
+        if len(split) != 7:
+            raise ValueError("split needs one flag per out-degree class (7)")
+        pol = _lib.Policy(1 if persistent else 0, int(chunk), (ctypes.c_int32 * 7)(*split), 1 if graph else 0)
         _lib.check(_lib.lib().pvt_dag_set_policy(self._h, ctypes.byref(pol)))
+
+    def autotune(self, kmax=None, W=None, out=None, stream=None):
+        """Pick the launch policy per out-degree class by timing three
+        candidates (pvt_dag_autotune); sets it on the dag and returns
+        (policy dict, ms [3][7] numpy array, counts tensor)."""
+        kmax, W = self._args(kmax, W)
+        out = self._out(None, kmax, W, out)
+        pol = _lib.Policy()
+        ms = np.zeros((3, 7), dtype=np.float32)
+        _lib.check(_lib.lib().pvt_dag_autotune(self._h, kmax, W, ctypes.c_void_p(out.data_ptr()),
+                                               _stream_handle(stream, self.device), ctypes.byref(pol),
+                                               ms.ctypes.data))
+        return (dict(persistent=bool(pol.persistent), chunk=pol.chunk, split=list(pol.split),
+                     graph=bool(pol.graph)), ms, out)
 
     def set_profiling(self, on: bool):
         _lib.check(_lib.lib().pvt_dag_set_profiling(self._h, 1 if on else 0))

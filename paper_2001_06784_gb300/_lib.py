@@ -28,7 +28,8 @@ class Stats(ctypes.Structure):
 
 class Policy(ctypes.Structure):
     """pvt_policy (include/pivoter.h)."""
-    _fields_ = [("persistent", ctypes.c_int32), ("chunk", ctypes.c_int32)]
+    _fields_ = [("persistent", ctypes.c_int32), ("chunk", ctypes.c_int32), ("split", ctypes.c_int32 * 7),
+                ("graph", ctypes.c_int32)]
 
 
 class ServerConfig(ctypes.Structure):
@@ -42,6 +43,7 @@ QUERY_GLOBAL, QUERY_VERTEX, QUERY_EDGE = 0, 1, 2
 # every symbol include/pivoter.h declares
 EXPORTS = ("pvt_orient", "pvt_dag_info", "pvt_count_global", "pvt_count_local_vertex",
            "pvt_count_local_edge", "pvt_dag_stats", "pvt_dag_set_profiling", "pvt_dag_set_policy",
+           "pvt_dag_get_policy", "pvt_dag_autotune",
            "pvt_count_global_noalloc", "pvt_server_create", "pvt_server_submit", "pvt_server_wait",
            "pvt_server_result", "pvt_server_destroy", "pvt_dag_free",
            "pvt_last_error")
@@ -73,6 +75,10 @@ def load(path: str = LIB_PATH):
     lib.pvt_dag_set_profiling.argtypes = [vp, i32]
     lib.pvt_dag_set_policy.restype = i32
     lib.pvt_dag_set_policy.argtypes = [vp, ctypes.POINTER(Policy)]
+    lib.pvt_dag_get_policy.restype = i32
+    lib.pvt_dag_get_policy.argtypes = [vp, ctypes.POINTER(Policy)]
+    lib.pvt_dag_autotune.restype = i32
+    lib.pvt_dag_autotune.argtypes = [vp, i32, i32, vp, vp, ctypes.POINTER(Policy), vp]
     lib.pvt_count_global_noalloc.restype = i32
     lib.pvt_count_global_noalloc.argtypes = [i64, vp, vp, i32, i32, i32, vp, vp]
     lib.pvt_server_create.restype = i32

@@ -41,14 +41,14 @@ pvt_status check_device(pvt_dag *g, cudaStream_t s, const char *what)
 
 void phase_begin(pvt_dag *g, int ph, cudaStream_t s)
 {
-    if (!g->profiling) return;
+    if (!g->profiling || g->capturing) return;
     cudaEventRecord(g->ev_t0[ph], s);
     g->phase_used[ph] = true;
 }
 
 void phase_end(pvt_dag *g, int ph, cudaStream_t s)
 {
-    if (g->profiling) cudaEventRecord(g->ev_t1[ph], s);
+    if (g->profiling && !g->capturing) cudaEventRecord(g->ev_t1[ph], s);
 }
 
 void stats_reset(pvt_dag *g)
@@ -61,6 +61,7 @@ static void dag_release(pvt_dag *g)
 {
     if (!g) return;
     cudaStreamSynchronize(0);
+    drop_graph(g);
     for (int c = 0; c < NCLASS; ++c) {
         if (g->side[c]) { cudaStreamSynchronize(g->side[c]); cudaStreamDestroy(g->side[c]); }
         if (g->ev_join[c]) cudaEventDestroy(g->ev_join[c]);
@@ -215,13 +216,32 @@ pvt_status pvt_dag_set_profiling(pvt_dag *dag, int32_t enable)
 
 pvt_status pvt_dag_set_policy(pvt_dag *dag, const pvt_policy *policy)
 {
-    if (!dag || !policy || (policy->persistent != 0 && policy->persistent != 1) || policy->chunk < 1 ||
-        policy->chunk > 32) {
+    bool ok = dag && policy && (policy->persistent == 0 || policy->persistent == 1) && policy->chunk >= 1 &&
+              policy->chunk <= 32 && (policy->graph == 0 || policy->graph == 1);
+    for (int c = 0; ok && c < NCLASS; ++c) ok = policy->split[c] == 0 || policy->split[c] == 1;
+    if (!ok) {
         set_error("pvt_dag_set_policy: invalid argument");
         return PVT_EINVAL;
     }
     dag->policy = *policy;
+    drop_graph(dag);
     return PVT_OK;
+}
+
+pvt_status pvt_dag_get_policy(const pvt_dag *dag, pvt_policy *out)
+{
+    if (!dag || !out) {
+        set_error("pvt_dag_get_policy: NULL argument");
+        return PVT_EINVAL;
+    }
+    *out = dag->policy;
+    return PVT_OK;
+}
+
+pvt_status pvt_dag_autotune(pvt_dag *dag, int32_t kmax, int32_t W, uint64_t *C, void *stream,
+                            pvt_policy *chosen, float *ms)
+{
+    return autotune(dag, kmax, W, C, (cudaStream_t)stream, chosen, ms);
 }
 
 void pvt_dag_free(pvt_dag *dag) { dag_release(dag); }

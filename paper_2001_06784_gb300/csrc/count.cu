@@ -2,6 +2,7 @@
 // batched form, the combine kernels and the allocation-free entry point.
 // The walk kernels themselves live in walk.cuh, instantiated per bitset
 // width in walk_nw*.cu.
+#include <algorithm>
 #include <mutex>
 #include <string>
 
@@ -159,12 +160,14 @@ static pvt_status ensure_binom(pvt_dag *g, int W, cudaStream_t s)
 template <int MODE>
 static pvt_status launch_all(pvt_dag *g, const CountArgs &A, cudaStream_t s)
 {
-    // heavy classes on side streams so that they overlap the light ones
-    PVT_CK(cudaEventRecord(g->ev_fork, s));
+    // heavy classes on side streams so that they overlap the light ones (or
+    // all on s, one after another, when the autotuner times them)
+    const bool serial = g->serial;
+    if (!serial) PVT_CK(cudaEventRecord(g->ev_fork, s));
     pvt_status st = PVT_OK;
     for (int c = NCLASS - 1; c >= 1 && st == PVT_OK; --c) {
-        cudaStream_t cs = g->side[c];
-        PVT_CK(cudaStreamWaitEvent(cs, g->ev_fork, 0));
+        cudaStream_t cs = serial ? s : g->side[c];
+        if (!serial) PVT_CK(cudaStreamWaitEvent(cs, g->ev_fork, 0));
         switch (c) {
             case 1: st = launch_class<1, MODE, MODE == MODE_GLOBAL>(g, A, c, cs); break;
             case 2: st = launch_class<2, MODE, MODE == MODE_GLOBAL>(g, A, c, cs); break;
@@ -173,9 +176,10 @@ static pvt_status launch_all(pvt_dag *g, const CountArgs &A, cudaStream_t s)
             case 5: st = launch_class<16, MODE, MODE == MODE_GLOBAL>(g, A, c, cs); break;
             case 6: st = launch_class<32, MODE, MODE == MODE_GLOBAL>(g, A, c, cs); break;
         }
-        PVT_CK(cudaEventRecord(g->ev_join[c], cs));
+        if (!serial) PVT_CK(cudaEventRecord(g->ev_join[c], cs));
     }
-    for (int c = NCLASS - 1; c >= 1; --c) PVT_CK(cudaStreamWaitEvent(s, g->ev_join[c], 0));
+    if (!serial)
+        for (int c = NCLASS - 1; c >= 1; --c) PVT_CK(cudaStreamWaitEvent(s, g->ev_join[c], 0));
     return st;
 }
 
@@ -217,11 +221,11 @@ static pvt_status check_args(pvt_dag *g, int32_t kmax, int32_t W, const void *ou
     return PVT_OK;
 }
 
-pvt_status count_global(pvt_dag *g, int32_t kmax, int32_t W, uint64_t *C, cudaStream_t s)
+// Every device operation of a global count, in stream order on s (also the
+// sequence recorded into a CUDA graph: no host synchronisation inside).
+static pvt_status enqueue_global(pvt_dag *g, int32_t kmax, int32_t W, uint64_t *C, cudaStream_t s)
 {
-    pvt_status st = check_args(g, kmax, W, C, 1, "pvt_count_global");
-    if (st != PVT_OK) return st;
-    begin_call(g);
+    pvt_status st;
     const int hstride = g->alpha + 2;
     if ((st = grow(g->hist, (size_t)hstride * hstride, s)) != PVT_OK) return st;
     if ((st = ensure_binom(g, W, s)) != PVT_OK) return st;
@@ -231,6 +235,7 @@ pvt_status count_global(pvt_dag *g, int32_t kmax, int32_t W, uint64_t *C, cudaSt
     PVT_CK(cudaMemsetAsync(g->d_stats, 0, 16 * sizeof(unsigned long long), s));
     if (g->class_cnt[0] && kmax >= 1) {
         k_add_leaf<<<1, 32, 0, s>>>(g->hist.p + hstride, (unsigned long long)g->class_cnt[0]);
+        PVT_CK(cudaGetLastError());
         g->stats.launches++;
     }
     CountArgs A{};
@@ -251,7 +256,126 @@ pvt_status count_global(pvt_dag *g, int32_t kmax, int32_t W, uint64_t *C, cudaSt
     PVT_CK(cudaGetLastError());
     phase_end(g, NPHASE - 1, s);
     g->stats.launches++;
-    return end_call(g, s, "pvt_count_global");
+    return PVT_OK;
+}
+
+void drop_graph(pvt_dag *g)
+{
+    if (g->graph_exec) cudaGraphExecDestroy(g->graph_exec);
+    g->graph_exec = nullptr;
+    g->graph_kmax = -1;
+    g->graph_W = 0;
+    g->graph_out = nullptr;
+    g->graph_launches = 0;
+}
+
+// Record the global count for (kmax, W, C) as a graph.  All scratch is sized
+// by the direct call that precedes this, so the recorded sequence allocates
+// nothing.  Recorded on the dag's own stream side[0] (the caller's stream
+// may be the legacy default stream, which cannot be captured).
+static pvt_status record_graph(pvt_dag *g, int32_t kmax, int32_t W, uint64_t *C)
+{
+    drop_graph(g);
+    cudaStream_t cs = g->side[0];
+    const pvt_stats keep = g->stats;
+    g->stats.launches = 0;
+    g->capturing = true;
+    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    pvt_status st = e == cudaSuccess ? enqueue_global(g, kmax, W, C, cs) : cuda_fail(e, "cudaStreamBeginCapture");
+    cudaGraph_t graph = nullptr;
+    if (e == cudaSuccess) {
+        cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
+        if (st == PVT_OK && e2 != cudaSuccess) st = cuda_fail(e2, "cudaStreamEndCapture");
+    }
+    g->capturing = false;
+    const uint64_t launches = g->stats.launches;
+    g->stats = keep;
+    if (st == PVT_OK) {
+        e = cudaGraphInstantiate(&g->graph_exec, graph, 0);
+        if (e != cudaSuccess) {
+            g->graph_exec = nullptr;
+            st = cuda_fail(e, "cudaGraphInstantiate");
+        }
+    }
+    if (graph) cudaGraphDestroy(graph);
+    if (st != PVT_OK) {
+        drop_graph(g);
+        return st;
+    }
+    g->graph_kmax = kmax;
+    g->graph_W = W;
+    g->graph_out = C;
+    g->graph_launches = launches;
+    return PVT_OK;
+}
+
+pvt_status count_global(pvt_dag *g, int32_t kmax, int32_t W, uint64_t *C, cudaStream_t s)
+{
+    pvt_status st = check_args(g, kmax, W, C, 1, "pvt_count_global");
+    if (st != PVT_OK) return st;
+    begin_call(g);
+    const bool use_graph = g->policy.graph != 0 && !g->serial;
+    if (use_graph && g->graph_exec && g->graph_kmax == kmax && g->graph_W == W && g->graph_out == C) {
+        PVT_CK(cudaGraphLaunch(g->graph_exec, s));
+        g->stats.launches = g->graph_launches;
+        return end_call(g, s, "pvt_count_global");
+    }
+    if ((st = enqueue_global(g, kmax, W, C, s)) != PVT_OK) return st;
+    if ((st = end_call(g, s, "pvt_count_global")) != PVT_OK) return st;
+    return use_graph ? record_graph(g, kmax, W, C) : PVT_OK;
+}
+
+// Per-class minimum over three candidate policies, classes timed one at a time.
+pvt_status autotune(pvt_dag *g, int32_t kmax, int32_t W, uint64_t *C, cudaStream_t s, pvt_policy *chosen,
+                    float *ms)
+{
+    if (!g || !chosen) {
+        set_error("pvt_dag_autotune: invalid argument");
+        return PVT_EINVAL;
+    }
+    static const pvt_policy cand[3] = {
+        {1, 4, {0, 0, 1, 1, 1, 1, 1}, 0},
+        {1, 1, {0, 0, 0, 0, 0, 0, 0}, 0},
+        {1, 16, {0, 0, 1, 1, 1, 1, 1}, 0},
+    };
+    const pvt_policy saved = g->policy;
+    const bool saved_prof = g->profiling;
+    float t[3][NCLASS] = {};
+    pvt_status st = PVT_OK;
+    drop_graph(g);
+    g->serial = true;
+    g->profiling = true;
+    for (int pass = 0; pass < 2 && st == PVT_OK; ++pass)
+        for (int c = 0; c < 3 && st == PVT_OK; ++c) {
+            g->policy = cand[c];
+            st = count_global(g, kmax, W, C, s);
+            for (int cls = 1; st == PVT_OK && cls < NCLASS; ++cls) {
+                float x = 0.f;
+                if (g->phase_used[1 + cls] &&
+                    cudaEventElapsedTime(&x, g->ev_t0[1 + cls], g->ev_t1[1 + cls]) == cudaSuccess)
+                    t[c][cls] = x;
+            }
+        }
+    g->serial = false;
+    g->profiling = saved_prof;
+    g->policy = saved;
+    if (st != PVT_OK) return st;
+    pvt_policy best = saved;
+    int bc = 0;
+    for (int c = 1; c < 3; ++c)
+        if (t[c][1] < t[bc][1]) bc = c;
+    best.chunk = cand[bc].chunk;
+    for (int cls = 0; cls < NCLASS; ++cls) {
+        if (cls < 2) { best.split[cls] = 0; continue; }
+        const float with = std::min(t[0][cls], t[2][cls]);
+        best.split[cls] = t[1][cls] < with ? 0 : 1;
+    }
+    g->policy = best;
+    *chosen = best;
+    if (ms)
+        for (int c = 0; c < 3; ++c)
+            for (int cls = 0; cls < NCLASS; ++cls) ms[c * NCLASS + cls] = t[c][cls];
+    return PVT_OK;
 }
 
 pvt_status count_local(pvt_dag *g, int32_t kmax, int32_t W, uint64_t *out, bool edge, cudaStream_t s)

@@ -72,7 +72,13 @@ struct pvt_dag {
     unsigned long long *h_stats = nullptr;  // pinned host copy
     pvt_stats stats = {};
     bool profiling = false;
-    pvt_policy policy = {1, 4};
+    pvt_policy policy = {1, 4, {0, 0, 1, 1, 1, 1, 1}, 0};
+    bool serial = false;           // launch the classes one after another on the caller's stream
+    bool capturing = false;        // recording a CUDA graph: no phase events
+    cudaGraphExec_t graph_exec = nullptr;  // recorded global count (policy.graph)
+    int graph_kmax = -1, graph_W = 0;
+    void *graph_out = nullptr;
+    uint64_t graph_launches = 0;
     cudaEvent_t ev_t0[pvt::NPHASE] = {}, ev_t1[pvt::NPHASE] = {};
     bool phase_used[pvt::NPHASE] = {};
     pvt::DevBuf<uint32_t> gstack[pvt::NCLASS];  // DFS stacks of the wide classes (global memory)
@@ -142,6 +148,9 @@ pvt_status ensure_edge_ids(pvt_dag *g, cudaStream_t s);
 pvt_status count_global(pvt_dag *g, int32_t kmax, int32_t W, uint64_t *C, cudaStream_t s);
 pvt_status count_local(pvt_dag *g, int32_t kmax, int32_t W, uint64_t *out, bool edge,
                        cudaStream_t s);
+pvt_status autotune(pvt_dag *g, int32_t kmax, int32_t W, uint64_t *C, cudaStream_t s, pvt_policy *chosen,
+                    float *ms);
+void drop_graph(pvt_dag *g);
 
 // Exclusive prefix sum of uint32 counts into int64 offsets (out has n+1 entries).
 pvt_status exclusive_scan_u32_i64(const uint32_t *in, int64_t *out, int64_t n, cudaStream_t s);

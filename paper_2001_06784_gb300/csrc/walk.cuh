@@ -899,8 +899,8 @@ pvt_status launch_class(pvt_dag *g, const CountArgs &base, int cls, cudaStream_t
     constexpr int WPB = warps_per_block<NW>();
     // the widest class always runs persistent warps (its stacks are per resident warp)
     const bool persist = g->policy.persistent != 0 || WarpWork<NW>::GSTACK;
-    // heavy classes of the global count split subtrees across warps
-    const bool split = persist && NW >= 2 && MODE == MODE_GLOBAL;
+    // heavy classes of the global count may split subtrees across warps
+    const bool split = persist && NW >= 2 && MODE == MODE_GLOBAL && g->policy.split[cls] != 0;
     auto kern = split ? k_count<NW, MODE, SHIST, true, true>
                       : (persist ? k_count<NW, MODE, SHIST, true, false> : k_count<NW, MODE, SHIST, false, false>);
     if (split) {

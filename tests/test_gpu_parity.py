@@ -154,10 +154,48 @@ def test_policies_agree(pvt, make):
     ref = oracle.count(rp, col)
     dag = gpu_dag(pvt, rp, col)
     out = {}
-    for persistent, chunk in [(True, 4), (False, 1), (True, 1), (True, 32)]:
-        dag.set_policy(persistent=persistent, chunk=chunk)
-        out[(persistent, chunk)] = pvt.to_ints(dag.count_global(kmax=ref["kmax"]))
+    nosplit, mixed = (0,) * 7, (0, 0, 1, 0, 1, 0, 1)
+    for persistent, chunk, split in [(True, 4, None), (False, 1, None), (True, 1, nosplit), (True, 32, mixed)]:
+        dag.set_policy(persistent=persistent, chunk=chunk, split=split)
+        out[(persistent, chunk, split)] = pvt.to_ints(dag.count_global(kmax=ref["kmax"]))
     assert all(v == ref["C"] for v in out.values())
+    dag.free()
+
+
+@pytest.mark.parametrize("make", [lambda: graphgen.workload("er2k_d20_clique30"),
+                                  lambda: graphs.clique_minus_random(300, 14, 7)])
+def test_graph_replay_and_autotune(pvt, make):
+    """Global counts replayed from a recorded CUDA graph equal the direct
+    launches (three replays, a new recording when kmax or the output
+    changes); the autotuner returns a valid policy and exact counts."""
+    import torch
+    rp, col = make()
+    ref = oracle.count(rp, col)
+    K = ref["kmax"]
+    dag = gpu_dag(pvt, rp, col)
+    dag.count_global(kmax=K)  # sizes the scratch and the Pascal table
+    direct = pvt.to_ints(dag.count_global(kmax=K))
+    launches = dag.stats()["launches"]
+    dag.set_policy(graph=True)
+    assert dag.policy()["graph"]
+    out = torch.empty((K + 1, dag.min_words), dtype=torch.int64, device="cuda:0")
+    for i in range(4):  # the first call launches directly and records; the rest replay
+        out.fill_(-1)
+        dag.count_global(kmax=K, out=out)
+        assert pvt.to_ints(out) == ref["C"] == direct, i
+        assert dag.stats()["launches"] == launches
+    assert pvt.to_ints(dag.count_global(kmax=K - 1)) == ref["C"][:K]
+    assert pvt.to_ints(dag.count_global(kmax=K)) == ref["C"]
+    pol, ms, C = dag.autotune(kmax=K)
+    assert pvt.to_ints(C) == ref["C"]
+    assert pol == dag.policy() and pol["graph"] and pol["chunk"] in (1, 4, 16)
+    assert all(x in (0, 1) for x in pol["split"]) and pol["split"][:2] == [0, 0]
+    assert ms.shape == (3, 7) and (ms >= 0).all() and ms[:, 1:].sum() > 0
+    for _ in range(2):
+        assert pvt.to_ints(dag.count_global(kmax=K)) == ref["C"]
+    with pytest.raises(pvt.PivoterError):
+        dag.set_policy(split=[2] * 7)
+    dag.free()
 
 
 # ------------------------------------------------------------ full sizes
