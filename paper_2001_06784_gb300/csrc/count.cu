@@ -597,14 +597,11 @@ __global__ void __launch_bounds__(32 * warps_per_block<NW>()) k_count_noalloc(Co
             break;
         }
         walk_root<NW, MODE_GLOBAL, false, false>(ww[wid], nullptr, A, lane, qi, wc);
+        wc.fold();
         if (vload(A.err) & (DERR_STACK | DERR_RANGE)) break;
     }
     (void)WPB;
-    if (lane == 0 && wc.nodes) {
-        atomicAdd(&A.stats[0], wc.nodes);
-        atomicAdd(&A.stats[1], wc.leaves);
-        atomicAdd(&A.stats[2], wc.words);
-    }
+    wc.flush(A.stats, -1, lane);
 }
 
 template <int NW>

@@ -159,6 +159,35 @@ constexpr uint32_t FRAME_WIDE = 1u, FRAME_COMPACT = 2u;
 // (where almost every leaf falls); other leaves go straight to the global one.
 constexpr int HIST_H = 32, HIST_P = 48;
 
+// Walk statistics.  nodes / leaves / words advance in step on every lane of
+// the warp; the x* fields count, per lane, the small subtrees that lane
+// closed in closed form (close_small), as the nodes, leaves and pivot words
+// the walk would have spent on them, until fold() adds their warp sums in.
+struct WalkCounters {
+    unsigned long long nodes = 0, leaves = 0, words = 0;
+    unsigned xnodes = 0, xleaves = 0, xwords = 0;
+    // after every walk item (all lanes)
+    __device__ __forceinline__ void fold()
+    {
+        nodes += __reduce_add_sync(0xFFFFFFFFu, xnodes);
+        leaves += __reduce_add_sync(0xFFFFFFFFu, xleaves);
+        words += __reduce_add_sync(0xFFFFFFFFu, xwords);
+        xnodes = xleaves = xwords = 0;
+    }
+    // add the warp's totals to stats[0..2] and, if cls >= 0, to stats[3 + cls]
+    // (all lanes)
+    __device__ __forceinline__ void flush(unsigned long long *stats, int cls, int lane)
+    {
+        fold();
+        if (lane == 0 && nodes) {
+            atomicAdd(&stats[0], nodes);
+            atomicAdd(&stats[1], leaves);
+            atomicAdd(&stats[2], words);
+            if (cls >= 0) atomicAdd(&stats[3 + cls], words);
+        }
+    }
+};
+
 template <bool SHIST>
 __device__ __forceinline__ void tally_leaf(unsigned long long *shist, const CountArgs &A, int lane, int h, int p)
 {
@@ -166,6 +195,43 @@ __device__ __forceinline__ void tally_leaf(unsigned long long *shist, const Coun
         if (SHIST && h < HIST_H && p < HIST_P) atomicAdd(&shist[h * HIST_P + p], 1ull);
         else atomicAdd(&A.hist[(size_t)h * A.hstride + p], 1ull);
     }
+}
+
+// Leaf tally by the calling lane alone (lanes tally independently).
+template <bool SHIST>
+__device__ __forceinline__ void tally_lane(unsigned long long *shist, const CountArgs &A, int h, int p)
+{
+    if (SHIST && h < HIST_H && p < HIST_P) atomicAdd(&shist[h * HIST_P + p], 1ull);
+    else atomicAdd(&A.hist[(size_t)h * A.hstride + p], 1ull);
+}
+
+// The subtree of a node with label S' of at most two members, reached with
+// (h, p), in closed form (global counts): |S'| = 0 is a leaf (h, p); a
+// single member or an adjacent pair is a clique, one leaf (h, p + |S'|); a
+// non-adjacent pair {a < b} takes a as pivot (a pivot leaf (h, p + 1)) and
+// holds b (a leaf (h + 1, p), cut when h + 1 > kmax).  Counts the nodes,
+// leaves and pivot words (wpm per member) the walk would have spent.
+// UNIFORM: every lane calls with the same arguments, lane 0 tallies.
+template <bool SHIST, bool UNIFORM>
+__device__ __forceinline__ void close_small(unsigned long long *shist, const CountArgs &A, int lane, int cs,
+                                            bool adjacent, int h, int p, unsigned wpm, WalkCounters &wc)
+{
+    if (UNIFORM) {
+        wc.nodes += 1 + (cs == 2 && !adjacent) + (cs == 2 && !adjacent && h + 1 <= A.kmax);
+        wc.leaves += 1 + (cs == 2 && !adjacent && h + 1 <= A.kmax);
+        wc.words += (unsigned long long)cs * wpm;
+    } else {
+        wc.xnodes += 1u + (cs == 2 && !adjacent) + (cs == 2 && !adjacent && h + 1 <= A.kmax);
+        wc.xleaves += 1u + (cs == 2 && !adjacent && h + 1 <= A.kmax);
+        wc.xwords += (unsigned)cs * wpm;
+    }
+    if (UNIFORM && lane != 0) return;
+    if (cs <= 1 || adjacent) {
+        tally_lane<SHIST>(shist, A, h, p + cs);
+        return;
+    }
+    tally_lane<SHIST>(shist, A, h, p + 1);  // the pivot leaf below the pair
+    if (h + 1 <= A.kmax) tally_lane<SHIST>(shist, A, h + 1, p);
 }
 
 // Donated frames must carry enough work to pay for the queue round trip.
@@ -214,9 +280,6 @@ __device__ __forceinline__ void frame_publish(const CountArgs &A, int lane, unsi
     if (lane == 0) atomicExch(A.qready + (t & (A.qcap - 1u)), t + 1u);
 }
 
-struct WalkCounters {
-    unsigned long long nodes = 0, leaves = 0, words = 0;
-};
 
 // Edge id of the edge between members a and b (local indices, d = root).
 template <int NW>
@@ -381,12 +444,24 @@ __device__ void compact_loop(WarpWork<NW> &Wk, unsigned long long *shist, const 
                 wc.leaves++;
                 tally(h, p + s1);
             } else {
-                closed = false;
                 const int piv = 31 - (int)(best & 31u);
                 const uint32_t rp = __shfl_sync(FULL, r1, piv);
-                const uint32_t R = S1 & ~rp & ~(1u << piv);
+                const uint32_t R0 = S1 & ~rp & ~(1u << piv);
+                // hold children: each lane of R0 forms its child's label; labels
+                // of at most two members are closed here, the rest are pushed
+                uint32_t R = 0;
+                if (R0 && h + 1 <= A.kmax) {
+                    const bool inR = (R0 >> lane) & 1u;
+                    const uint32_t child = inR ? (r1 & S1 & ~(R0 & ((1u << lane) - 1u))) : 0u;
+                    const int cs = __popc(child);
+                    const uint32_t ra = __shfl_sync(FULL, r1, (__ffs(child) - 1) & 31);
+                    if (inR && cs <= 2)
+                        close_small<SHIST, false>(shist, A, lane, cs, (ra >> ((31 - __clz(child)) & 31)) & 1u, h + 1, p,
+                                                  1u, wc);
+                    R = __ballot_sync(FULL, inR && cs > 2);
+                }
                 const int nR = __popc(R);
-                if (nR > 0 && h + 1 <= A.kmax) {
+                if (nR > 0) {
                     if (SPLIT && bot > 0 && top + nR > 33) {
                         __syncwarp();
                         for (int t = lane; t < top - bot; t += 32) {
@@ -403,9 +478,9 @@ __device__ void compact_loop(WarpWork<NW> &Wk, unsigned long long *shist, const 
                     }
                     __syncwarp();
                     if ((R >> lane) & 1u) {
-                        const uint32_t below = R & ((1u << lane) - 1u);
-                        const int f = top + __popc(below);
-                        Wk.stk1[f] = r1 & S1 & ~below;
+                        const uint32_t low = (1u << lane) - 1u;
+                        const int f = top + __popc(R & low);
+                        Wk.stk1[f] = r1 & S1 & ~(R0 & low);
                         Wk.hp1[f] = ((uint32_t)(h + 1) << 16) | (uint32_t)p;
                     }
                     top += nR;
@@ -445,8 +520,17 @@ __device__ void compact_loop(WarpWork<NW> &Wk, unsigned long long *shist, const 
                         }
                     }
                 }
-                S1 = rp & S1;
-                p += 1;
+                // the pivot child N(S, piv): closed at once if it has at most two members
+                const uint32_t P1 = rp & S1;
+                const int ps = __popc(P1);
+                if (ps <= 2) {
+                    const uint32_t ra = __shfl_sync(FULL, r1, (__ffs(P1) - 1) & 31);
+                    close_small<SHIST, true>(shist, A, lane, ps, (ra >> ((31 - __clz(P1)) & 31)) & 1u, h, p + 1, 1u, wc);
+                } else {
+                    closed = false;
+                    S1 = P1;
+                    p += 1;
+                }
             }
         }
         if (!closed) continue;
@@ -652,7 +736,6 @@ __device__ void walk_root(WarpWork<NW> &Wk, unsigned long long *shist, const Cou
                     local_leaf<NW, MODE>(Wk, A, lane, r, rbeg, d, h, p + s, depth, S);
                 }
             } else {
-                closed = false;
                 uint32_t R[NW], P[NW];
                 int nR = 0;
 #pragma unroll
@@ -678,23 +761,47 @@ __device__ void walk_root(WarpWork<NW> &Wk, unsigned long long *shist, const Cou
                         return;
                     }
                     __syncwarp();  // every lane is done reading the last popped frame
+                    // hold child of member j*32+lane: N(S, v) minus the earlier
+                    // members of R; global counts close labels of at most two
+                    // members here and push the rest
                     int before = 0;
+                    const uint32_t low = (1u << lane) - 1u;
 #pragma unroll
                     for (int j = 0; j < NW; ++j) {
-                        if ((R[j] >> lane) & 1u) {
-                            const uint32_t low = (1u << lane) - 1u;
-                            const int f = top + before + __popc(R[j] & low);
+                        const bool inR = (R[j] >> lane) & 1u;
+                        bool push = inR;
+                        if (MODE == MODE_GLOBAL && inR) {
+                            int cs = 0, a = 0, b = 0;
 #pragma unroll
                             for (int w = 0; w < NW; ++w) {
-                                uint32_t below = w < j ? R[w] : (w == j ? (R[j] & low) : 0u);
+                                const uint32_t below = w < j ? R[w] : (w == j ? (R[j] & low) : 0u);
+                                const uint32_t cw = row(j, w) & S[w] & ~below;
+                                if (cw) {
+                                    if (cs == 0) a = w * 32 + __ffs(cw) - 1;
+                                    b = w * 32 + 31 - __clz(cw);
+                                }
+                                cs += __popc(cw);
+                            }
+                            if (cs <= 2) {
+                                const bool adj = cs == 2 && ((Wk.adj[a * RS + (b >> 5)] >> (b & 31)) & 1u);
+                                close_small<SHIST, false>(shist, A, lane, cs, adj, h + 1, p, NW, wc);
+                                push = false;
+                            }
+                        }
+                        const uint32_t pushed = __ballot_sync(FULL, push);
+                        if (push) {
+                            const int f = top + before + __popc(pushed & low);
+#pragma unroll
+                            for (int w = 0; w < NW; ++w) {
+                                const uint32_t below = w < j ? R[w] : (w == j ? (R[j] & low) : 0u);
                                 Wk.stk()[f * NW + w] = row(j, w) & S[w] & ~below;
                             }
                             Wk.hp[f] = ((uint32_t)(h + 1) << 16) | (uint32_t)p;
                             if (MODE != MODE_GLOBAL) Wk.lk[f] = (uint16_t)(j * 32 + lane);
                         }
-                        before += __popc(R[j]);
+                        before += __popc(pushed);
                     }
-                    top += nR;
+                    top += before;
                     __syncwarp();  // pushed frames visible to every lane
                     if (SPLIT && clk.nodes >= clk.next) {
                         clk.next = clk.nodes + DONATE_EVERY;
@@ -711,11 +818,29 @@ __device__ void walk_root(WarpWork<NW> &Wk, unsigned long long *shist, const Cou
                         bot += ndon;
                     }
                 }
-                // continue into the pivot child N(S, piv)
+                // continue into the pivot child N(S, piv), or close it at once
+                // (global counts) if it has at most two members
+                int ps = 0, a = 0, b = 0;
+                if (MODE == MODE_GLOBAL) {
 #pragma unroll
-                for (int w = 0; w < NW; ++w) S[w] = P[w];
-                p += 1;
-                link = (uint16_t)(LINK_PIVOT | piv);
+                    for (int w = 0; w < NW; ++w) {
+                        if (P[w]) {
+                            if (ps == 0) a = w * 32 + __ffs(P[w]) - 1;
+                            b = w * 32 + 31 - __clz(P[w]);
+                        }
+                        ps += __popc(P[w]);
+                    }
+                }
+                if (MODE == MODE_GLOBAL && ps <= 2) {
+                    const bool adj = ps == 2 && ((Wk.adj[a * RS + (b >> 5)] >> (b & 31)) & 1u);
+                    close_small<SHIST, true>(shist, A, lane, ps, adj, h, p + 1, NW, wc);
+                } else {
+                    closed = false;
+#pragma unroll
+                    for (int w = 0; w < NW; ++w) S[w] = P[w];
+                    p += 1;
+                    link = (uint16_t)(LINK_PIVOT | piv);
+                }
             }
         }
         if (!closed) continue;
@@ -828,6 +953,7 @@ __global__ void __launch_bounds__(32 * warps_per_block<NW>())
             } else {
                 walk_root<NW, MODE, SHIST, true>(ww[wid], shist, A, lane, A.roots[v], wc, v, nullptr);
             }
+            wc.fold();
             __syncwarp();
             if (lane == 0) atomicSub(A.qctl + Q_OUT, 1u);
         }
@@ -844,16 +970,12 @@ __global__ void __launch_bounds__(32 * warps_per_block<NW>())
         }
         if (qi >= A.nroots) break;
         walk_root<NW, MODE, SHIST, false>(ww[wid], shist, A, lane, A.roots[qi], wc);
+        wc.fold();
         ++qi;
         if (!PERSIST) break;
         if (*(volatile unsigned *)A.err & (DERR_STACK | DERR_RANGE)) break;
     }
-    if (lane == 0 && wc.nodes) {
-        atomicAdd(&A.stats[0], wc.nodes);
-        atomicAdd(&A.stats[1], wc.leaves);
-        atomicAdd(&A.stats[2], wc.words);
-        atomicAdd(&A.stats[3 + A.cls], wc.words);
-    }
+    wc.flush(A.stats, A.cls, lane);
     if (SHIST) {
         __syncthreads();
         for (int i = threadIdx.x; i < HIST_H * HIST_P; i += blockDim.x) {
@@ -989,14 +1111,11 @@ __global__ void __launch_bounds__(32 * warps_per_block<NW>())
         A.err = err;
         A.stats = stats;
         walk_root<NW, MODE, false, false>(ww[wid], nullptr, A, lane, (uint32_t)e, wc);
+        wc.fold();
         if (vload(err) & (DERR_STACK | DERR_RANGE)) break;
     }
     (void)WPB;
-    if (lane == 0 && wc.nodes) {
-        atomicAdd(&stats[0], wc.nodes);
-        atomicAdd(&stats[1], wc.leaves);
-        atomicAdd(&stats[2], wc.words);
-    }
+    wc.flush(stats, -1, lane);
 }
 
 template <int NW, int MODE>
