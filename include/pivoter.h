@@ -83,6 +83,16 @@ pvt_status pvt_dag_info(const pvt_dag *dag, int64_t *n, int64_t *m, int32_t *alp
                         int32_t *min_words);
 
 /*
+ * Core numbers found by the peel (Sec. 3.2: the degeneracy order removes a
+ * vertex of smallest residual degree; the core number of v is the largest k
+ * such that v lies in a subgraph of minimum degree k).  Unlike the removal
+ * order, core numbers do not depend on how ties are broken.
+ *   core    device uint32[n] (caller-owned), written in full on `stream`
+ * Errors: PVT_EINVAL (NULL dag, or NULL core with n > 0), PVT_ECUDA.
+ */
+pvt_status pvt_dag_cores(const pvt_dag *dag, uint32_t *core, void *stream);
+
+/*
  * Global counts C_k for k = 0..kmax (Sec. 3.1; Alg. 2, the C_{|H|+i} update;
  * correctness: proof of Thm. main).  Each root vertex r explores the SCT
  * below its child N+(r) (Alg. 1) depth first; every root-to-leaf path T with

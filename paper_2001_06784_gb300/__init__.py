@@ -58,6 +58,13 @@ class Dag:
             raise ValueError(f"out must be a contiguous int64 tensor of shape {shape}")
         return out
 
+    def cores(self, stream=None):
+        """Core number of every vertex (uint32 values in an int32 tensor [n])."""
+        out = torch.empty(self.n, dtype=torch.int32, device=self.device)
+        _lib.check(_lib.lib().pvt_dag_cores(self._h, ctypes.c_void_p(out.data_ptr() if self.n else 0),
+                                            _stream_handle(stream, self.device)))
+        return out
+
     def count_global(self, kmax=None, W=None, out=None, stream=None):
         """C_k for k = 0..kmax as an int64 tensor [kmax+1, W] of 64-bit words
         (little-endian, reinterpret as unsigned)."""

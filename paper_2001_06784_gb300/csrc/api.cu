@@ -171,6 +171,18 @@ pvt_status pvt_dag_info(const pvt_dag *dag, int64_t *n, int64_t *m, int32_t *alp
     return PVT_OK;
 }
 
+pvt_status pvt_dag_cores(const pvt_dag *dag, uint32_t *core, void *stream)
+{
+    if (!dag || (!core && dag->n > 0)) {
+        set_error("pvt_dag_cores: invalid argument");
+        return PVT_EINVAL;
+    }
+    if (dag->n > 0)
+        PVT_CK(cudaMemcpyAsync(core, dag->core, (size_t)dag->n * sizeof(uint32_t), cudaMemcpyDeviceToDevice,
+                               (cudaStream_t)stream));
+    return PVT_OK;
+}
+
 pvt_status pvt_count_global(pvt_dag *dag, int32_t kmax, int32_t W, uint64_t *C, void *stream)
 {
     return count_global(dag, kmax, W, C, (cudaStream_t)stream);

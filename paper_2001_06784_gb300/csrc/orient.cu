@@ -61,15 +61,15 @@ struct PeelState {
     unsigned pad0[31];
     unsigned tail;        // vertices pushed onto the removal queue so far
     unsigned pad1[31];
-    unsigned pending;     // pushed but not yet processed (this level)
+    unsigned done;        // queue entries fully processed so far
     unsigned pad2[31];
-    unsigned min_deg[2];  // smallest residual degree among remaining vertices (by level parity)
-    unsigned remain[2];   // vertices not yet removed (by level parity)
+    unsigned min_next[2]; // lower bound of the next level's smallest residual degree (by level parity)
+    unsigned alive_cnt[2];// length of the alive list being built (by level parity)
     unsigned bar_count;   // grid barrier arrivals
     unsigned bar_gen;     // grid barrier generation
     unsigned rounds;      // grid barriers passed (diagnostic)
     unsigned levels;      // levels visited (diagnostic)
-    unsigned top_level;   // degeneracy: the last level k
+    unsigned top_level;   // degeneracy: the last level k at which a vertex was removed
 };
 
 constexpr unsigned long long BARRIER_LIMIT_NS = 4000000000ull;  // 4 s
@@ -118,131 +118,171 @@ __device__ bool grid_barrier(PeelState *st, unsigned *err)
 
 // k-core peeling, exact by level, asynchronous within a level.
 //
-// Level k starts when every remaining vertex has residual degree >= k (k is
-// the smallest residual degree).  All remaining vertices of degree <= k are
-// pushed onto one global removal queue; warps then take queue entries one at
-// a time and lower the residual degrees of their neighbours that are still
-// present; a neighbour whose degree falls to k is pushed at once.  The level
-// ends when nothing pushed is left unprocessed.  Every vertex is pushed
-// exactly once, so its queue position is a unique removal time: rnd[v].
+// Level k removes every remaining vertex whose residual degree is (or falls
+// to) at most k; k runs upward from the smallest degree.  A level has two
+// phases, each closed by a grid barrier:
+//   scan     every vertex of the alive list (all vertices at level 0) that
+//            is still present is pushed onto one global removal queue if its
+//            degree is <= k, else appended to the next alive list;
+//   cascade  warps take queue entries one at a time and lower the residual
+//            degree of every neighbour of the entry; the one decrement that
+//            takes a neighbour from k+1 to k pushes it at once.  The level
+//            ends when every pushed entry has been processed (done == tail).
+// Every vertex is pushed exactly once, so its queue position is a unique
+// removal time: rnd[v].  Neighbours already removed are decremented too: a
+// removed vertex's degree is <= k and only falls, so it can never be pushed
+// again, and skipping the presence test saves a dependent load per hop.
+// The next level's k is the smallest degree seen above k -- at the scan and
+// at every decrement -- which never exceeds the true smallest residual
+// degree, so no level with removals is skipped (a level can be empty).
 // Out-degree bound: a neighbour pushed after v never lowered deg[v] (v was
 // already removed when it was processed), so at v's push deg[v] <= k counts
 // all of v's later neighbours.
 __global__ void __launch_bounds__(1024) k_peel(int64_t n, const int64_t *__restrict__ rp,
                                                const uint32_t *__restrict__ col, uint32_t *deg,
-                                               uint32_t *rnd, uint32_t *core, uint32_t *lq, PeelState *st,
-                                               unsigned *err)
+                                               uint32_t *rnd, uint32_t *core, uint32_t *lq, uint32_t *alive,
+                                               PeelState *st, unsigned *err)
 {
-    const int lane = threadIdx.x & 31;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
     volatile PeelState *vst = st;
 
-    for (int64_t v = tid; v < n; v += nthreads) {
-        deg[v] = (uint32_t)(rp[v + 1] - rp[v]);
-        rnd[v] = NOT_REMOVED;
-        lq[v] = EMPTY;
+    if (tid == 0) {
+        st->min_next[0] = st->min_next[1] = NOT_REMOVED;
+        st->alive_cnt[0] = st->alive_cnt[1] = 0;
     }
-    if (tid == 0) { st->min_deg[0] = NOT_REMOVED; st->remain[0] = 0; }
+    if (!grid_barrier(st, err)) return;
+    {
+        unsigned mine = NOT_REMOVED;
+        for (int64_t v = tid; v < n; v += nthreads) {
+            const uint32_t dv = (uint32_t)(rp[v + 1] - rp[v]);
+            deg[v] = dv;
+            rnd[v] = NOT_REMOVED;
+            lq[v] = EMPTY;
+            mine = min(mine, dv);
+        }
+        mine = __reduce_min_sync(FULL, mine);
+        if (lane == 0 && mine != NOT_REMOVED) atomicMin(&st->min_next[0], mine);
+    }
     if (!grid_barrier(st, err)) return;
 
-    unsigned k = 0, level = 0;
-    unsigned claim = EMPTY;  // lane 0: this warp's claimed queue position, kept across levels
-    for (;;) {
-        // ---- level start: smallest residual degree among remaining vertices
-        const unsigned lp = level & 1u;
-        {
-            unsigned mine = NOT_REMOVED, cntr = 0;
-            for (int64_t v = tid; v < n; v += nthreads)
-                if (rnd[v] == NOT_REMOVED) { mine = min(mine, deg[v]); ++cntr; }
-            for (int o = 16; o; o >>= 1) {
-                mine = min(mine, __shfl_xor_sync(FULL, mine, o));
-                cntr += __shfl_xor_sync(FULL, cntr, o);
+    unsigned top = 0;
+    for (unsigned level = 0;; ++level) {
+        const unsigned q = level & 1u;
+        // done only moves during a cascade: every thread reads the same value
+        // here, and it equals tail (the last cascade ended with done == tail)
+        const unsigned t_start = vst->done;
+        if ((int64_t)t_start >= n) break;  // every vertex removed
+        const unsigned k = vst->min_next[q];
+        const int64_t cnt = level == 0 ? n : (int64_t)vst->alive_cnt[q];
+        // ---- scan: push present vertices of degree <= k, keep the others
+        unsigned mnext = NOT_REMOVED;
+        for (int64_t base = tid - lane; base < cnt; base += nthreads) {
+            const int64_t i = base + lane;
+            uint32_t v = 0;
+            bool present = false;
+            uint32_t dv = 0;
+            if (i < cnt) {
+                v = level == 0 ? (uint32_t)i : alive[(q ? n : 0) + i];
+                present = rnd[v] == NOT_REMOVED;
+                if (present) dv = deg[v];
             }
-            if (lane == 0 && mine != NOT_REMOVED) { atomicMin(&st->min_deg[lp], mine); atomicAdd(&st->remain[lp], cntr); }
+            const bool take = present && dv <= k, keep = present && dv > k;
+            const unsigned bt = __ballot_sync(FULL, take), bk = __ballot_sync(FULL, keep);
+            const unsigned below = (1u << lane) - 1u;
+            if (bt) {
+                unsigned at = 0;
+                if (lane == 0) at = atomicAdd(&st->tail, (unsigned)__popc(bt));
+                at = __shfl_sync(FULL, at, 0);
+                if (take) {
+                    const unsigned pos = at + __popc(bt & below);
+                    rnd[v] = pos;
+                    core[v] = k;
+                    lq[pos] = v;
+                }
+            }
+            if (bk) {
+                unsigned at = 0;
+                if (lane == 0) at = atomicAdd(&st->alive_cnt[q ^ 1u], (unsigned)__popc(bk));
+                at = __shfl_sync(FULL, at, 0);
+                if (keep) {
+                    alive[(q ? 0 : n) + at + __popc(bk & below)] = v;
+                    mnext = min(mnext, dv);
+                }
+            }
         }
         if (!grid_barrier(st, err)) return;
-        const unsigned md = vst->min_deg[lp];
-        if (md == NOT_REMOVED) {  // every vertex removed
-            if (tid == 0) st->top_level = k;
-            break;
-        }
-        k = max(k, md);
         if (tid == 0) {
             st->levels++;
-            st->min_deg[lp ^ 1u] = NOT_REMOVED;  // next level's counters (last read before the barrier above)
-            st->remain[lp ^ 1u] = 0;
+            st->min_next[q] = NOT_REMOVED;  // read by every thread above; next written at level + 1
+            st->alive_cnt[q] = 0;
         }
-        ++level;
-        // ---- push every remaining vertex of degree <= k (warp-aggregated)
-        for (int64_t base = tid - lane; base < n; base += nthreads) {
-            const int64_t v = base + lane;
-            const bool take = v < n && rnd[v] == NOT_REMOVED && deg[v] <= k;
-            const unsigned b = __ballot_sync(FULL, take);
-            if (!b) continue;
-            unsigned at = 0;
-            if (lane == 0) {
-                at = atomicAdd(&st->tail, (unsigned)__popc(b));
-                atomicAdd(&st->pending, (unsigned)__popc(b));
-            }
-            at = __shfl_sync(FULL, at, 0);
-            if (take) {
-                const unsigned i = at + __popc(b & ((1u << lane) - 1u));
-                rnd[v] = i;
-                core[v] = k;
-                lq[i] = (uint32_t)v;
-            }
-        }
-        if (!grid_barrier(st, err)) return;
-        // ---- cascade: take queue entries until nothing is pending
-        for (;;) {
-            int got = 0;  // 1: vertex in `v`, 2: level done, 3: error
-            uint32_t v = 0;
-            if (lane == 0) {
-                if (claim == EMPTY) claim = atomicAdd(&st->head, 1u);
-                unsigned nap = 32, last = 0xFFFFFFFFu;
-                unsigned long long t0 = global_ns();
-                for (;;) {
-                    if (claim < (uint64_t)n) {
-                        const uint32_t x = *(volatile uint32_t *)(lq + claim);
-                        if (x != EMPTY) { v = x; got = 1; break; }
+        // ---- cascade, on as many warps per block as the waiting entries need
+        // (at least two per block; warps that read the counters late may see
+        // a different count, which changes only how many warps take part)
+        const unsigned waiting = vst->tail - vst->done;
+        const unsigned want = min(max(waiting > (1u << 28) ? (1u << 30) : 4u * waiting, 256u), (unsigned)(nthreads >> 5));
+        const unsigned per_block = (want + gridDim.x - 1) / gridDim.x;
+        if ((unsigned)wid < per_block) {
+            unsigned claim = EMPTY;  // lane 0: this warp's queue position
+            for (;;) {
+                int got = 0;  // 1: vertex in `v`, 2: level done, 3: error
+                uint32_t v = 0;
+                if (lane == 0) {
+                    if (claim == EMPTY) claim = atomicAdd(&st->head, 1u);
+                    unsigned spins = 0, last = 0xFFFFFFFFu;
+                    unsigned long long t0 = 0;
+                    for (;;) {
+                        if (claim < (uint64_t)n) {
+                            const uint32_t x = *(volatile uint32_t *)(lq + claim);
+                            if (x != EMPTY) { v = x; got = 1; break; }
+                        }
+                        if ((++spins & 7u) == 0) {
+                            // quiescent once every pushed entry is processed; read
+                            // done before tail (done <= tail at all times)
+                            const unsigned dn = vst->done;
+                            __threadfence();
+                            if (vst->tail == dn) { got = 2; break; }
+                            if (*(volatile unsigned *)err & DERR_TIMEOUT) { got = 3; break; }
+                            if (dn != last) { last = dn; t0 = global_ns(); }
+                            else if (global_ns() - t0 > CASCADE_LIMIT_NS) { atomicOr(err, DERR_TIMEOUT); got = 3; break; }
+                        }
+                        __nanosleep(spins < 64 ? 20 : 200);
                     }
-                    const unsigned pend = vst->pending;
-                    if (pend == 0) { got = 2; break; }
-                    if (*(volatile unsigned *)err & DERR_TIMEOUT) { got = 3; break; }
-                    if (pend != last) { last = pend; t0 = global_ns(); }
-                    else if (global_ns() - t0 > CASCADE_LIMIT_NS) { atomicOr(err, DERR_TIMEOUT); got = 3; break; }
-                    __nanosleep(nap);
-                    nap = min(nap * 2u, 1024u);
+                    if (got == 1) claim = EMPTY;
                 }
-                if (got == 1) claim = EMPTY;
-            }
-            got = __shfl_sync(FULL, got, 0);
-            if (got == 3) return;
-            if (got == 2) break;
-            v = __shfl_sync(FULL, v, 0);
-            for (int64_t j = rp[v] + lane; j < rp[v + 1]; j += 32) {
-                const uint32_t u = col[j];
-                if (rnd[u] == NOT_REMOVED) {
+                got = __shfl_sync(FULL, got, 0);
+                if (got == 3) return;
+                if (got == 2) break;
+                v = __shfl_sync(FULL, v, 0);
+                for (int64_t j = rp[v] + lane; j < rp[v + 1]; j += 32) {
+                    const uint32_t u = col[j];
                     const unsigned old = atomicSub(&deg[u], 1u);
                     if (old == k + 1) {
-                        atomicAdd(&st->pending, 1u);
-                        const unsigned i = atomicAdd(&st->tail, 1u);
-                        rnd[u] = i;
+                        const unsigned pos = atomicAdd(&st->tail, 1u);
+                        rnd[u] = pos;
                         core[u] = k;
-                        __threadfence();
-                        *(volatile uint32_t *)(lq + i) = u;
+                        *(volatile uint32_t *)(lq + pos) = u;
+                    } else if (old > k + 1) {
+                        mnext = min(mnext, old - 1);
                     }
                 }
-            }
-            __syncwarp();
-            if (lane == 0) {
-                __threadfence();
-                atomicSub(&st->pending, 1u);
+                __syncwarp();
+                if (lane == 0) {
+                    __threadfence();  // this entry's pushes are counted before it is done
+                    atomicAdd(&st->done, 1u);
+                }
             }
         }
+        mnext = __reduce_min_sync(FULL, mnext);
+        if (lane == 0 && mnext != NOT_REMOVED) atomicMin(&st->min_next[q ^ 1u], mnext);
         if (!grid_barrier(st, err)) return;
+        const unsigned t_end = vst->done;
+        if (t_end > t_start) top = k;
+        if (tid == 0) st->head = t_end;  // drop claims past the end of the queue
     }
+    if (tid == 0) st->top_level = top;
 }
 
 // ------------------------------------------------------------ orientation
@@ -496,12 +536,13 @@ pvt_status orient_build(pvt_dag *g, uint32_t flags, cudaStream_t s)
         if (st != PVT_OK) return st;
     }
 
-    uint32_t *deg = nullptr, *lq = nullptr, *odeg = nullptr;
+    uint32_t *deg = nullptr, *lq = nullptr, *odeg = nullptr, *alive = nullptr;
     unsigned *dhist = nullptr;
     PeelState *pst = nullptr;
     const size_t nb = (size_t)std::max<int64_t>(n, 1) * sizeof(uint32_t);
     PVT_CK(cudaMallocAsync(&deg, nb, s));
     PVT_CK(cudaMallocAsync(&lq, nb, s));
+    PVT_CK(cudaMallocAsync(&alive, 2 * nb, s));
     PVT_CK(cudaMallocAsync(&pst, sizeof(PeelState) + sizeof(unsigned), s));
     PVT_CK(cudaMallocAsync(&g->rnd, nb, s));
     PVT_CK(cudaMallocAsync(&g->core, nb, s));
@@ -521,7 +562,7 @@ pvt_status orient_build(pvt_dag *g, uint32_t flags, cudaStream_t s)
         const uint32_t *col = g->col;
         uint32_t *rnd = g->rnd, *core = g->core;
         unsigned *err = g->d_err;
-        void *args[] = {&nn, &rp, &col, &deg, &rnd, &core, &lq, &pst, &err};
+        void *args[] = {&nn, &rp, &col, &deg, &rnd, &core, &lq, &alive, &pst, &err};
         phase_begin(g, 0, s);
         PVT_CK(cudaLaunchCooperativeKernel((void *)k_peel, dim3(g->num_sms * per_sm), dim3(1024), args,
                                            0, s));
@@ -596,6 +637,7 @@ pvt_status orient_build(pvt_dag *g, uint32_t flags, cudaStream_t s)
 
     PVT_CK(cudaFreeAsync(deg, s));
     PVT_CK(cudaFreeAsync(lq, s));
+    PVT_CK(cudaFreeAsync(alive, s));
     PVT_CK(cudaFreeAsync(pst, s));
     PVT_CK(cudaFreeAsync(odeg, s));
     PVT_CK(cudaFreeAsync(dhist, s));

@@ -213,6 +213,24 @@ def test_workload_full_global(pvt, name):
     assert got[1] == n and got[2] == m
 
 
+@pytest.mark.parametrize("make", [
+    lambda: graphs.complete(40), lambda: graphs.multipartite([3, 5, 7, 2]), lambda: graphs.gnp(300, 0.1, 3),
+    lambda: graphgen.from_edges(5, []), lambda: graphs.disjoint_cliques([1, 2, 33, 70]),
+    lambda: graphgen.workload("er2k_d20_clique30"), lambda: graphgen.workload("cl1m_m10m_b2.1_comm500"),
+    lambda: graphgen.workload("cl500k_m8m_b2.3_clq200")])
+def test_core_numbers(pvt, make):
+    """Core numbers of the device peel equal the oracle's (sequential bucket
+    peel): they do not depend on the removal order within a level, so the
+    comparison is exact; the reported alpha is the largest of them."""
+    rp, col = make()
+    _, core, _ = oracle.orient(rp, col)
+    dag = gpu_dag(pvt, rp, col)
+    got = dag.cores().cpu().numpy().view(np.uint32)
+    assert np.array_equal(got, core)
+    assert dag.alpha == (int(core.max()) if len(core) else 0)
+    dag.free()
+
+
 def test_workload_local_sampled(pvt):
     """Per-vertex / per-edge tables at full size (500k vertices, 8M edges),
     checked on sampled rows one by one: c_k(v) = C_{k-1} of the subgraph
