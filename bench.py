@@ -31,6 +31,10 @@ L2_FLUSH_BYTES = 256 << 20   # > 129 MB L2
 POPC_PER_CLK_PER_SM = 16     # 32-bit population count issue rate per SM per clock
 SM_COUNT = 152
 SM_MAX_MHZ = 2070.0
+# DRAM bytes (read + write) per launch of the walk kernels, from the ncu
+# captures summarised under profiles/; an entry must be removed whenever its
+# kernel changes, so that the bench line reports null instead of a stale figure
+NCU_DRAM_BYTES = {"walk_d64": 21650432 + 348672}
 
 
 def parse():
@@ -462,7 +466,7 @@ def main():
     peak = POPC_PER_CLK_PER_SM * SM_COUNT * SM_MAX_MHZ * 1e6 / 1e9  # Gop/s
     achieved = words / (mean_ph[dom] / 1000.0) / 1e9
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gop/s", "frac": achieved / peak,
-                "traffic": None, "kernel": f"k_count<{dom}>", "kernel_ms": mean_ph[dom],
+                "traffic": NCU_DRAM_BYTES.get(dom), "kernel": f"k_count<{dom}>", "kernel_ms": mean_ph[dom],
                 "op": "32-bit AND+POPC word pairs of pivot selection",
                 "peak_source": f"{POPC_PER_CLK_PER_SM} POPC/clk/SM x {SM_COUNT} SMs x {SM_MAX_MHZ:.0f} MHz"}
 
