@@ -208,6 +208,20 @@ def run_local(args, dev, flush):
         ms = float(np.mean(times))
         res[kind] = {"ms_per_step": ms, "edges_per_s": m / (ms / 1000.0), "table_bytes": int(t.nbytes),
                      "sum_identity": tot == want}
+        # f_k(b) over the table at the k the paper plots (5, 10, ..., 25)
+        dist = {}
+        for k in (5, 10, 15, 20, 25):
+            if k > omega:
+                continue
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            vals, cnts = pvt.local_distribution(out, k)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            f_mass = int(cnts.sum().item())
+            dist[str(k)] = {"ms": e0.elapsed_time(e1), "distinct": int(len(cnts)), "rows": f_mass}
+        res[kind]["distribution"] = dist
         del out, t
     return res
 

@@ -129,6 +129,27 @@ pvt_status pvt_count_local_edge(pvt_dag *dag, int32_t kmax, int32_t W, uint64_t 
                                 void *stream);
 
 /*
+ * Frequency distribution of one column of a local count table (the
+ * per-vertex clique distributions of the experiments, "Demonstrations of
+ * Pivoter": f_k(b) = the number of vertices that take part in exactly b
+ * k-cliques; over a per-edge table, the number of edges).
+ *   table       device uint64[rows][K][W], as written by
+ *               pvt_count_local_vertex / pvt_count_local_edge (read only)
+ *   rows, K, W  its shape; rows <= 2^32 - 2, 1 <= W <= 20
+ *   k           the column, 0 <= k < K
+ *   values      device uint64[rows][W] (caller-owned): the distinct values b
+ *               of column k, W words each, least significant first
+ *   counts      device uint64[rows] (caller-owned): f_k(b) for each value
+ *   n_distinct  host: the number of (value, count) pairs written
+ * Pairs come in no particular order; the counts sum to rows.  The call
+ * allocates stream-ordered scratch (12 bytes per hash slot, at least
+ * 2 * rows slots) and returns once the pairs are written.
+ * Errors: PVT_EINVAL (argument out of range), PVT_ENOMEM, PVT_ECUDA.
+ */
+pvt_status pvt_local_distribution(const uint64_t *table, int64_t rows, int32_t K, int32_t W, int32_t k,
+                                  uint64_t *values, uint64_t *counts, int64_t *n_distinct, void *stream);
+
+/*
  * Statistics of the last orient or count call on a dag (no counterpart in
  * the paper's algorithms; its Fig. treesize reports SCT sizes).  Tree
  * figures are of the walk the device performed: nodes popped from the DFS

@@ -149,6 +149,19 @@ def count(row_ptr, col, *, kmax: int = -1, vertex: bool = False, edge: bool = Fa
     return out
 
 
+def frequency(table, k: int) -> dict:
+    """f_k(b): how many rows of a local count table (limb array
+    [rows][K][nl] from ``count``) take each value b in column k -- the
+    per-vertex clique distributions of the paper's experiments
+    ("Demonstrations of Pivoter"), or the same over edges.  Returns
+    {b: f_k(b)} with exact integer keys."""
+    col = np.asarray(table)[:, k, :]
+    if len(col) == 0:
+        return {}
+    vals, cnt = np.unique(col, axis=0, return_counts=True)
+    return {to_int(v): int(c) for v, c in zip(vals, cnt)}
+
+
 def paths(row_ptr, col, cap: int = 1 << 22):
     """Every root-to-leaf path T of the SCT as ``(H(T), P(T))`` vertex lists,
     in walk order (tiny graphs only)."""

@@ -21,7 +21,7 @@ import torch
 from . import _lib
 from ._lib import PVT_PROFILE, PVT_VALIDATE, PivoterError
 
-__all__ = ["orient", "Dag", "Server", "to_ints", "count_global_host", "PivoterError"]
+__all__ = ["orient", "Dag", "Server", "local_distribution", "to_ints", "count_global_host", "PivoterError"]
 
 
 def _stream_handle(stream, device):
@@ -234,6 +234,24 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+def local_distribution(table: torch.Tensor, k: int, stream=None):
+    """f_k(b) over the rows of a local count table (int64 tensor
+    [rows, K, W] from count_local_vertex / count_local_edge): returns
+    (values int64 [D, W], counts int64 [D]), the D distinct values b of
+    column k and how many rows take each, in no particular order."""
+    if table.dim() != 3 or table.dtype != torch.int64 or not table.is_cuda or not table.is_contiguous():
+        raise ValueError("table must be a contiguous CUDA int64 tensor [rows, K, W]")
+    rows, K, W = table.shape
+    values = torch.empty((max(rows, 1), W), dtype=torch.int64, device=table.device)
+    counts = torch.empty(max(rows, 1), dtype=torch.int64, device=table.device)
+    nd = ctypes.c_int64()
+    _lib.check(_lib.lib().pvt_local_distribution(ctypes.c_void_p(table.data_ptr() if rows else 0), rows, K, W,
+                                                 int(k), ctypes.c_void_p(values.data_ptr()),
+                                                 ctypes.c_void_p(counts.data_ptr()), ctypes.byref(nd),
+                                                 _stream_handle(stream, table.device)))
+    return values[:nd.value], counts[:nd.value]
 
 
 def to_ints(t):

@@ -41,7 +41,7 @@ class ServerConfig(ctypes.Structure):
 QUERY_GLOBAL, QUERY_VERTEX, QUERY_EDGE = 0, 1, 2
 
 # every symbol include/pivoter.h declares
-EXPORTS = ("pvt_orient", "pvt_dag_info", "pvt_dag_cores", "pvt_count_global", "pvt_count_local_vertex",
+EXPORTS = ("pvt_orient", "pvt_dag_info", "pvt_dag_cores", "pvt_local_distribution", "pvt_count_global", "pvt_count_local_vertex",
            "pvt_count_local_edge", "pvt_dag_stats", "pvt_dag_set_profiling", "pvt_dag_set_policy",
            "pvt_dag_get_policy", "pvt_dag_autotune",
            "pvt_count_global_noalloc", "pvt_server_create", "pvt_server_submit", "pvt_server_wait",
@@ -65,6 +65,8 @@ def load(path: str = LIB_PATH):
     lib.pvt_dag_info.restype = i32
     lib.pvt_dag_info.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(i32),
                                  ctypes.POINTER(i32)]
+    lib.pvt_local_distribution.restype = i32
+    lib.pvt_local_distribution.argtypes = [vp, i64, i32, i32, i32, vp, vp, ctypes.POINTER(i64), vp]
     lib.pvt_dag_cores.restype = i32
     lib.pvt_dag_cores.argtypes = [vp, vp, vp]
     for fn in ("pvt_count_global", "pvt_count_local_vertex", "pvt_count_local_edge"):

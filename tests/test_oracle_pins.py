@@ -291,3 +291,47 @@ def test_limb_overflow_is_reported():
     with pytest.raises(RuntimeError, match="overflow"):
         oracle.count(rp, col, nl=1)
     assert oracle.count(rp, col, nl=2)["C"][20] == math.comb(40, 20)
+
+
+# ------------------------------------------ f_k(b), "Demonstrations of Pivoter"
+
+@pytest.mark.parametrize("sizes", [[5], [4, 7, 7], [1, 3, 9, 12]])
+def test_frequency_closed_form(sizes):
+    """Disjoint cliques: a vertex of K_a lies in C(a-1, k-1) k-cliques and an
+    edge of K_a in C(a-2, k-2)."""
+    rp, col = graphs.disjoint_cliques(sizes)
+    r = oracle.count(rp, col, vertex=True, edge=True)
+    for k in range(r["kmax"] + 1):
+        want_v, want_e = {}, {}
+        for a in sizes:
+            b = math.comb(a - 1, k - 1) if k >= 1 else 0
+            want_v[b] = want_v.get(b, 0) + a
+            if a >= 2:
+                b = math.comb(a - 2, k - 2) if k >= 2 else 0
+                want_e[b] = want_e.get(b, 0) + math.comb(a, 2)
+        assert oracle.frequency(r["cv"], k) == want_v
+        assert oracle.frequency(r["ce"], k) == want_e
+
+
+@pytest.mark.parametrize("n,p,seed", [(12, 0.5, 1), (16, 0.6, 2), (20, 0.45, 3)])
+def test_frequency_bruteforce(n, p, seed):
+    """f_k from brute-force per-vertex / per-edge clique counts; the mass and
+    first moment identities sum f_k(b) = rows, sum b f_k(b) = k C_k (vertices)
+    or C(k,2) C_k (edges)."""
+    rp, col = graphs.gnp(n, p, seed)
+    r = oracle.count(rp, col, vertex=True, edge=True)
+    K = r["kmax"]
+    _, bv, be = brute_counts(rp, col, K)
+    m = len(col) // 2
+    for k in range(K + 1):
+        fv = oracle.frequency(r["cv"], k)
+        fe = oracle.frequency(r["ce"], k)
+        want_v, want_e = {}, {}
+        for row in bv:
+            want_v[row[k]] = want_v.get(row[k], 0) + 1
+        for row in be:
+            want_e[row[k]] = want_e.get(row[k], 0) + 1
+        assert fv == want_v and fe == want_e
+        assert sum(fv.values()) == n and sum(fe.values()) == m
+        assert sum(b * c for b, c in fv.items()) == k * r["C"][k]
+        assert sum(b * c for b, c in fe.items()) == math.comb(k, 2) * r["C"][k]
