@@ -70,7 +70,21 @@ struct PeelState {
     unsigned rounds;      // grid barriers passed (diagnostic)
     unsigned levels;      // levels visited (diagnostic)
     unsigned top_level;   // degeneracy: the last level k at which a vertex was removed
+    // hand-over to the one-block finish (k_peel_tail)
+    unsigned stop;        // 1: the grid peel stopped with few vertices left
+    unsigned stop_k;      // k of the first level left to the finish
+    unsigned stop_q;      // parity of that level (which alive list)
+    unsigned stop_all;    // 1: stopped at level 0 (every vertex is alive, no list)
+    unsigned stop_cnt;    // entries of that alive list
+    unsigned res_n;       // vertices left (local ids 0..res_n-1)
+    unsigned long long res_edges;  // entries of their residual adjacency
 };
+
+// The grid peel hands the levels over to one block once at most this many
+// vertices are alive: their degrees, removal queue and row offsets then fit
+// in shared memory, and a level costs block barriers instead of grid ones.
+constexpr unsigned TAIL_MAX = 16384;
+constexpr int TAIL_THREADS = 1024;
 
 constexpr unsigned long long BARRIER_LIMIT_NS = 4000000000ull;  // 4 s
 constexpr unsigned long long CASCADE_LIMIT_NS = 4000000000ull;  // 4 s without progress
@@ -141,7 +155,7 @@ __device__ bool grid_barrier(PeelState *st, unsigned *err)
 __global__ void __launch_bounds__(1024) k_peel(int64_t n, const int64_t *__restrict__ rp,
                                                const uint32_t *__restrict__ col, uint32_t *deg,
                                                uint32_t *rnd, uint32_t *core, uint32_t *lq, uint32_t *alive,
-                                               PeelState *st, unsigned *err)
+                                               PeelState *st, unsigned tail_max, unsigned *err)
 {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -176,6 +190,16 @@ __global__ void __launch_bounds__(1024) k_peel(int64_t n, const int64_t *__restr
         if ((int64_t)t_start >= n) break;  // every vertex removed
         const unsigned k = vst->min_next[q];
         const int64_t cnt = level == 0 ? n : (int64_t)vst->alive_cnt[q];
+        if (cnt <= (int64_t)tail_max) {  // the rest in one block (k_peel_tail)
+            if (tid == 0) {
+                st->stop = 1;
+                st->stop_k = k;
+                st->stop_q = q;
+                st->stop_all = level == 0;
+                st->stop_cnt = (unsigned)cnt;
+            }
+            break;
+        }
         // ---- scan: push present vertices of degree <= k, keep the others
         unsigned mnext = NOT_REMOVED;
         for (int64_t base = tid - lane; base < cnt; base += nthreads) {
@@ -283,6 +307,213 @@ __global__ void __launch_bounds__(1024) k_peel(int64_t n, const int64_t *__restr
         if (tid == 0) st->head = t_end;  // drop claims past the end of the queue
     }
     if (tid == 0) st->top_level = top;
+}
+
+// ------------------------------------------------ one-block finish of the peel
+
+__device__ void block_scan_u32_i64(const uint32_t *in, int64_t *out, int64_t n);
+
+// Vertices still present where the grid peel stopped get local ids
+// 0..res_n-1 (tv: local -> global, loc: global -> local) and their residual
+// degrees: deg[v] counts exactly the present neighbours, since every removed
+// vertex has been processed.
+__global__ void k_tail_compact(int64_t n, const uint32_t *__restrict__ alive, const uint32_t *__restrict__ rnd,
+                               const uint32_t *__restrict__ deg, uint32_t *loc, uint32_t *tv, uint32_t *rdeg,
+                               PeelState *st)
+{
+    if (!st->stop) return;
+    const int64_t cnt = st->stop_cnt;
+    const bool all = st->stop_all != 0;
+    if (!all && st->stop_q) alive += n;
+    const int lane = threadIdx.x & 31;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t base = blockIdx.x * (int64_t)blockDim.x + threadIdx.x - lane; base < cnt; base += stride) {
+        const int64_t i = base + lane;
+        uint32_t v = 0;
+        bool present = false;
+        if (i < cnt) {
+            v = all ? (uint32_t)i : alive[i];
+            present = rnd[v] == NOT_REMOVED;
+        }
+        const unsigned b = __ballot_sync(FULL, present);
+        if (!b) continue;
+        unsigned at = 0;
+        if (lane == 0) at = atomicAdd(&st->res_n, (unsigned)__popc(b));
+        at = __shfl_sync(FULL, at, 0);
+        if (present) {
+            const unsigned id = at + __popc(b & ((1u << lane) - 1u));
+            loc[v] = id;
+            tv[id] = v;
+            rdeg[id] = deg[v];
+        }
+    }
+}
+
+// Row offsets of the residual adjacency (one block).
+__global__ void k_tail_scan(const uint32_t *rdeg, int64_t *roff, PeelState *st)
+{
+    if (!st->stop) return;
+    const unsigned R = st->res_n;
+    block_scan_u32_i64(rdeg, roff, R);
+    if (threadIdx.x == 0) st->res_edges = (unsigned long long)roff[R];
+}
+
+// Residual adjacency: local ids of the present neighbours (warp per vertex).
+__global__ void k_tail_fill(const int64_t *__restrict__ rp, const uint32_t *__restrict__ col,
+                            const uint32_t *__restrict__ rnd, const uint32_t *__restrict__ loc,
+                            const uint32_t *__restrict__ tv, const int64_t *__restrict__ roff, uint32_t *rcol,
+                            const PeelState *st, unsigned *err)
+{
+    if (!st->stop) return;
+    const int lane = threadIdx.x & 31;
+    const unsigned R = st->res_n;
+    const int64_t w0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t i = w0; i < (int64_t)R; i += nw) {
+        const uint32_t v = tv[i];
+        const int64_t beg = rp[v], end = rp[v + 1], out = roff[i], cap = roff[i + 1] - out;
+        int64_t pos = 0;
+        for (int64_t j0 = beg; j0 < end; j0 += 32) {
+            const int64_t j = j0 + lane;
+            uint32_t u = 0;
+            bool keep = false;
+            if (j < end) {
+                u = col[j];
+                keep = rnd[u] == NOT_REMOVED;
+            }
+            const unsigned b = __ballot_sync(FULL, keep);
+            if (keep) {
+                const int64_t at = pos + __popc(b & ((1u << lane) - 1u));
+                if (at < cap) rcol[out + at] = loc[u];
+            }
+            pos += __popc(b);
+        }
+        if (lane == 0 && pos != cap) atomicOr(err, DERR_RANGE);
+    }
+}
+
+// The remaining levels in one block, same rules as k_peel (scan, then a
+// cascade that ends when done == tail) on block-shared state: residual
+// degrees, the removal queue and the row offsets live in shared memory,
+// the residual adjacency (local ids) in global memory.  Removal times
+// continue the grid peel's numbering.
+__global__ void __launch_bounds__(TAIL_THREADS) k_peel_tail(const int64_t *__restrict__ roff,
+                                                            const uint32_t *__restrict__ rcol,
+                                                            const uint32_t *__restrict__ rdeg,
+                                                            const uint32_t *__restrict__ tv, uint32_t *rnd,
+                                                            uint32_t *core, PeelState *st, unsigned *err)
+{
+    extern __shared__ __align__(16) uint32_t tsm[];
+    uint32_t *sdeg = tsm, *sq = tsm + TAIL_MAX, *soff = tsm + 2 * TAIL_MAX, *sgone = tsm + 3 * TAIL_MAX + 1;
+    __shared__ unsigned s_head, s_tail, s_done, s_min[2], s_bad;
+    volatile unsigned *vq = sq;
+    const int lane = threadIdx.x & 31;
+    if (!st->stop) return;
+    const unsigned R = st->res_n;
+    if (R > TAIL_MAX) {
+        if (threadIdx.x == 0) atomicOr(err, DERR_RANGE);
+        return;
+    }
+    const unsigned base = st->done;  // removals so far (grid peel)
+    for (unsigned i = threadIdx.x; i < R; i += blockDim.x) {
+        sdeg[i] = rdeg[i];
+        sq[i] = EMPTY;
+        soff[i] = (uint32_t)roff[i];
+    }
+    for (unsigned i = threadIdx.x; i < (R + 31) / 32; i += blockDim.x) sgone[i] = 0;
+    if (threadIdx.x == 0) {
+        soff[R] = (uint32_t)roff[R];
+        s_head = s_tail = s_done = 0;
+        s_min[0] = st->stop_k;
+        s_min[1] = NOT_REMOVED;
+        s_bad = 0;
+    }
+    __syncthreads();
+    unsigned top = st->top_level, levels = 0;
+    auto push = [&](unsigned i, unsigned k) {
+        atomicOr(&sgone[i >> 5], 1u << (i & 31));
+        const unsigned pos = atomicAdd(&s_tail, 1u);
+        rnd[tv[i]] = base + pos;
+        core[tv[i]] = k;
+        __threadfence_block();
+        vq[pos] = i;
+    };
+    for (unsigned level = 0;; ++level) {
+        const unsigned q = level & 1u;
+        const unsigned t_start = *(volatile unsigned *)&s_done;
+        if (t_start >= R) break;
+        const unsigned k = s_min[q];
+        ++levels;
+        unsigned mnext = NOT_REMOVED;
+        // ---- scan
+        for (unsigned i = threadIdx.x; i < R; i += blockDim.x) {
+            if ((sgone[i >> 5] >> (i & 31)) & 1u) continue;
+            const unsigned d = sdeg[i];
+            if (d <= k) push(i, k);
+            else mnext = min(mnext, d);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) s_min[q] = NOT_REMOVED;  // read above by every thread
+        // ---- cascade (every warp)
+        {
+            unsigned claim = EMPTY;
+            for (;;) {
+                int got = 0;  // 1: entry in i, 2: level done, 3: error
+                unsigned i = 0;
+                if (lane == 0) {
+                    if (claim == EMPTY) claim = atomicAdd(&s_head, 1u);
+                    unsigned spins = 0, last = EMPTY;
+                    unsigned long long t0 = 0;
+                    for (;;) {
+                        if (claim < R) {
+                            const unsigned x = vq[claim];
+                            if (x != EMPTY) { i = x; got = 1; break; }
+                        }
+                        const unsigned dn = *(volatile unsigned *)&s_done;
+                        __threadfence_block();
+                        if (*(volatile unsigned *)&s_tail == dn) { got = 2; break; }
+                        if ((++spins & 63u) == 0) {
+                            if (*(volatile unsigned *)&s_bad) { got = 3; break; }
+                            if (dn != last) { last = dn; t0 = global_ns(); }
+                            else if (global_ns() - t0 > CASCADE_LIMIT_NS) {
+                                atomicOr(err, DERR_TIMEOUT);
+                                s_bad = 1;
+                                got = 3;
+                                break;
+                            }
+                        }
+                        if (spins > 16) __nanosleep(32);
+                    }
+                    if (got == 1) claim = EMPTY;
+                }
+                got = __shfl_sync(FULL, got, 0);
+                if (got != 1) break;
+                i = __shfl_sync(FULL, i, 0);
+                for (unsigned j = soff[i] + lane; j < soff[i + 1]; j += 32) {
+                    const uint32_t u = rcol[j];
+                    const unsigned old = atomicSub(&sdeg[u], 1u);
+                    if (old == k + 1) push(u, k);
+                    else if (old > k + 1) mnext = min(mnext, old - 1);
+                }
+                __syncwarp();
+                if (lane == 0) {
+                    __threadfence_block();  // this entry's pushes are counted before it is done
+                    atomicAdd(&s_done, 1u);
+                }
+            }
+        }
+        mnext = __reduce_min_sync(FULL, mnext);
+        if (lane == 0 && mnext != NOT_REMOVED) atomicMin(&s_min[q ^ 1u], mnext);
+        __syncthreads();
+        if (s_bad) return;
+        if (s_done > t_start) top = k;
+        __syncthreads();  // every thread has read s_done before the claims are reset
+        if (threadIdx.x == 0) s_head = s_tail;
+    }
+    if (threadIdx.x == 0) {
+        st->top_level = top;
+        st->levels += levels;
+    }
 }
 
 // ------------------------------------------------------------ orientation
@@ -537,6 +768,8 @@ pvt_status orient_build(pvt_dag *g, uint32_t flags, cudaStream_t s)
     }
 
     uint32_t *deg = nullptr, *lq = nullptr, *odeg = nullptr, *alive = nullptr;
+    uint32_t *tv = nullptr, *rdeg = nullptr, *rcol = nullptr;
+    int64_t *roff = nullptr;
     unsigned *dhist = nullptr;
     PeelState *pst = nullptr;
     const size_t nb = (size_t)std::max<int64_t>(n, 1) * sizeof(uint32_t);
@@ -562,12 +795,27 @@ pvt_status orient_build(pvt_dag *g, uint32_t flags, cudaStream_t s)
         const uint32_t *col = g->col;
         uint32_t *rnd = g->rnd, *core = g->core;
         unsigned *err = g->d_err;
-        void *args[] = {&nn, &rp, &col, &deg, &rnd, &core, &lq, &alive, &pst, &err};
+        unsigned tail_max = TAIL_MAX;
+        void *args[] = {&nn, &rp, &col, &deg, &rnd, &core, &lq, &alive, &pst, &tail_max, &err};
         phase_begin(g, 0, s);
         PVT_CK(cudaLaunchCooperativeKernel((void *)k_peel, dim3(g->num_sms * per_sm), dim3(1024), args,
                                            0, s));
+        // the levels left once at most TAIL_MAX vertices are alive: one block
+        // on the compacted residual graph (each kernel returns at once if the
+        // grid peel finished by itself); lq is free by now and holds local ids
+        PVT_CK(cudaMallocAsync(&tv, (size_t)TAIL_MAX * sizeof(uint32_t), s));
+        PVT_CK(cudaMallocAsync(&rdeg, (size_t)TAIL_MAX * sizeof(uint32_t), s));
+        PVT_CK(cudaMallocAsync(&roff, (size_t)(TAIL_MAX + 1) * sizeof(int64_t), s));
+        PVT_CK(cudaMallocAsync(&rcol, (size_t)std::max<int64_t>(g->nnz, 1) * sizeof(uint32_t), s));
+        k_tail_compact<<<(TAIL_MAX + 255) / 256, 256, 0, s>>>(n, alive, g->rnd, deg, lq, tv, rdeg, pst);
+        k_tail_scan<<<1, 1024, 0, s>>>(rdeg, roff, pst);
+        k_tail_fill<<<g->num_sms * 8, 256, 0, s>>>(g->row_ptr, g->col, g->rnd, lq, tv, roff, rcol, pst, g->d_err);
+        constexpr size_t tail_smem = (3 * (size_t)TAIL_MAX + 1 + TAIL_MAX / 32) * sizeof(uint32_t);
+        PVT_CK(cudaFuncSetAttribute(k_peel_tail, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tail_smem));
+        k_peel_tail<<<1, TAIL_THREADS, tail_smem, s>>>(roff, rcol, rdeg, tv, g->rnd, g->core, pst, g->d_err);
+        PVT_CK(cudaGetLastError());
         phase_end(g, 0, s);
-        g->stats.launches++;
+        g->stats.launches += 5;
     }
     phase_begin(g, 1, s);
 
@@ -638,6 +886,10 @@ pvt_status orient_build(pvt_dag *g, uint32_t flags, cudaStream_t s)
     PVT_CK(cudaFreeAsync(deg, s));
     PVT_CK(cudaFreeAsync(lq, s));
     PVT_CK(cudaFreeAsync(alive, s));
+    PVT_CK(cudaFreeAsync(tv, s));
+    PVT_CK(cudaFreeAsync(rdeg, s));
+    PVT_CK(cudaFreeAsync(roff, s));
+    PVT_CK(cudaFreeAsync(rcol, s));
     PVT_CK(cudaFreeAsync(pst, s));
     PVT_CK(cudaFreeAsync(odeg, s));
     PVT_CK(cudaFreeAsync(dhist, s));
