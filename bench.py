@@ -34,7 +34,7 @@ SM_MAX_MHZ = 2070.0
 # DRAM bytes (read + write) per launch of the walk kernels, from the ncu
 # captures summarised under profiles/; an entry must be removed whenever its
 # kernel changes, so that the bench line reports null instead of a stale figure
-NCU_DRAM_BYTES = {"walk_d64": 21650432 + 348672}
+NCU_DRAM_BYTES = {}
 
 
 def parse():
@@ -106,6 +106,23 @@ class ClockSampler:
         return {"sm_mhz": float(np.median(sm)) if sm else None,
                 "sm_max_mhz": max(smax) if smax else None,
                 "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def max_over_ranks(x: float, device) -> float:
+    """The largest of every rank's x (all ranks call this; one rank: x)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: float, world: int, seconds_max: float) -> float:
+    """Whole-job throughput of N replicas: the units all ranks processed over
+    the slowest rank's time."""
+    return world * units_per_rank / seconds_max
 
 
 def run_reference(args, ws, rank):
@@ -412,13 +429,9 @@ def main():
         dag.free()
     torch.cuda.synchronize(dev)
     clocks = sampler.stop()
-    total_s = sum(step_ms) / 1000.0
-    if ws > 1:
-        t = torch.tensor([total_s], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_s = float(t.item())
+    total_s = max_over_ranks(sum(step_ms) / 1000.0, dev)
     ms_per_step = total_s * 1000.0 / args.steps
-    value = ws * m * args.steps / total_s
+    value = whole_job_rate(m * args.steps, ws, total_s)
     C_words = C.cpu()
     C_ints = pvt.to_ints(C_words)
     assert tuned_C == C_ints, "autotuner run and timed steps differ"
@@ -440,7 +453,7 @@ def main():
         plain_ms.append(e0.elapsed_time(e1))
         dag.free()
     assert pvt.to_ints(Cp) == C_ints, "plain and persistent forms differ"
-    plain_value = ws * m * len(plain_ms) / (sum(plain_ms) / 1000.0)
+    plain_value = whole_job_rate(m * len(plain_ms), ws, max_over_ranks(sum(plain_ms) / 1000.0, dev))
 
     # ---- end to end through the public API: pinned host CSR in, counts out
     C_host = torch.empty((kmax + 1, W), dtype=torch.int64).pin_memory()
@@ -463,20 +476,18 @@ def main():
             e2e_ms.append(e0.elapsed_time(e1))
         dag.free()
         del rp_x, col_x
-    e2e_s = sum(e2e_ms) / 1000.0
-    if ws > 1:
-        t = torch.tensor([e2e_s], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e_value = ws * m * len(e2e_ms) / e2e_s
+    e2e_s = max_over_ranks(sum(e2e_ms) / 1000.0, dev)
+    e2e_value = whole_job_rate(m * len(e2e_ms), ws, e2e_s)
     assert pvt.to_ints(C_host) == C_ints, "end-to-end result differs from the device-resident one"
 
     # ---- roofline of the dominant kernel (the SCT walk of the busiest class)
     mean_ph = {k: float(np.mean([p[k] for p in phase_ms])) for k in phase_ms[0]}
     walk_keys = [k for k in mean_ph if k.startswith("walk_")]
     dom = max(walk_keys, key=lambda k: mean_ph[k])
-    cls = pvt.Dag.PHASES.index(dom) - 1  # out-degree class of that kernel
-    words = walk["class_words"][cls]
+    if dom == "walk_frames":
+        words = walk["frame_words"]
+    else:
+        words = walk["class_words"][pvt.Dag.PHASES.index(dom) - 1]  # out-degree class of that kernel
     peak = POPC_PER_CLK_PER_SM * SM_COUNT * SM_MAX_MHZ * 1e6 / 1e9  # Gop/s
     achieved = words / (mean_ph[dom] / 1000.0) / 1e9
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gop/s", "frac": achieved / peak,
@@ -503,7 +514,8 @@ def main():
            "clocks": clocks,
            "phases_ms": mean_ph,
            "sct": {"nodes": walk["sct_nodes"], "leaves": walk["sct_leaves"], "pivot_words": walk["pivot_words"],
-                   "roots_per_class": walk["roots"], "pivot_words_per_class": walk["class_words"]},
+                   "roots_per_class": walk["roots"], "pivot_words_per_class": walk["class_words"],
+                   "frame_words": walk["frame_words"], "frames": walk["frames"]},
            "peel": {"rounds": so["peel_rounds"], "levels": so["peel_levels"]}}
 
     # ---- launch cost: direct launches vs replay of the recorded CUDA graph

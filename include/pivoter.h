@@ -129,6 +129,33 @@ pvt_status pvt_count_local_edge(pvt_dag *dag, int32_t kmax, int32_t W, uint64_t 
                                 void *stream);
 
 /*
+ * Global counts in pieces, for checkpointing long counts.  Every clique is
+ * counted once, at its first vertex in the orientation, and the roots are
+ * independent (Sec. 4, "Parallel version"), so the (h, p) histogram of
+ * root-to-leaf paths over a set of roots is the whole state of a count:
+ * histograms of disjoint root sets add up, and C_k = sum over (h, p) of
+ * hist[h][p] * C(p, k - h) (proof of Thm. main) turns the sum into counts.
+ *   pvt_count_hist  walks the roots r with begin <= r < end (vertex ids;
+ *                   end is clipped to n) and ADDS their path counts to
+ *                   hist, device uint64[(alpha+2)][(alpha+2)] (row h,
+ *                   column p; caller-owned, not cleared); branches with
+ *                   more than kmax hold links are cut as in
+ *                   pvt_count_global.  The call synchronises `stream` once
+ *                   to size the range.
+ *   pvt_combine_hist  C (device uint64[kmax+1][W]) from such a histogram;
+ *                   kmax must not exceed the one the histogram was built
+ *                   with; W as pvt_count_global.
+ * Copying hist to the host after any range and back before the next is a
+ * checkpoint; the histogram of disjoint ranges counted on different GPUs
+ * (each with its own dag of the same graph) is their sum.
+ * Errors: PVT_EINVAL (NULL dag or hist, kmax < 0, begin < 0, end < begin),
+ * others as pvt_count_global.
+ */
+pvt_status pvt_count_hist(pvt_dag *dag, int64_t begin, int64_t end, int32_t kmax, uint64_t *hist, void *stream);
+pvt_status pvt_combine_hist(pvt_dag *dag, const uint64_t *hist, int32_t kmax, int32_t W, uint64_t *C,
+                            void *stream);
+
+/*
  * Frequency distribution of one column of a local count table (the
  * per-vertex clique distributions of the experiments, "Demonstrations of
  * Pivoter": f_k(b) = the number of vertices that take part in exactly b
@@ -158,8 +185,8 @@ pvt_status pvt_local_distribution(const uint64_t *table, int64_t rows, int32_t K
  * pivot selection (|S| * ceil(d/32) per internal node).  ms[] holds device
  * time per phase when profiling is on (else zeros): [0] peel, [1] orient
  * (DAG CSR and root classes), [2..7] the walk kernels of out-degree classes
- * <=32, <=64, <=128, <=256, <=512, <=1024, [8] combine/finish.  Phases of
- * different classes overlap in time.
+ * <=32, <=64, <=128, <=256, <=512, <=1024, [8] combine/finish, [9] the
+ * frame walk (policy.frames).  Phases of different classes overlap in time.
  */
 typedef struct pvt_stats {
     uint64_t sct_nodes;
@@ -167,8 +194,12 @@ typedef struct pvt_stats {
     uint64_t pivot_words;
     uint64_t launches;      /* kernels launched by the call */
     uint64_t roots[7];      /* roots per out-degree class (0, <=32, ..., <=1024) */
-    uint64_t class_words[7];/* pivot_words split by out-degree class */
-    float ms[9];
+    uint64_t class_words[7];/* pivot_words of the class kernels (walk of labels > 32
+                               members only when frames are on) */
+    uint64_t frame_words;   /* pivot_words of the frame walk (policy.frames) */
+    uint64_t frames;        /* frames the wide walks emitted (above the buffer:
+                               walked in place) */
+    float ms[10];
     uint32_t peel_rounds;   /* orient: grid-wide barriers of the peel */
     uint32_t peel_levels;   /* orient: distinct core levels visited */
 } pvt_stats;
@@ -194,6 +225,13 @@ pvt_status pvt_dag_set_profiling(pvt_dag *dag, int32_t enable);
  *               0 keeps one warp per root.  Only classes with out-degree
  *               above 32 can split, and only in the persistent form; local
  *               counts never split.  Default {0, 0, 1, 1, 1, 1, 1}.
+ *   frames      1 (default): global counts run in two phases -- the kernels
+ *               of the classes above 32 walk only labels of more than 32
+ *               members and emit every smaller label's subtree as a
+ *               self-contained frame (its one-word adjacency rows), which a
+ *               second kernel with small per-warp state, and so many more
+ *               resident warps, walks for all classes; 0: each class walks
+ *               its small labels itself.  Persistent form only.
  *   graph       1: pvt_count_global records its launch sequence as a CUDA
  *               graph at the first call with a given (kmax, W, C) and
  *               replays it at later calls with the same three (the dag's
@@ -206,6 +244,7 @@ typedef struct pvt_policy {
     int32_t chunk;
     int32_t split[7];
     int32_t graph;
+    int32_t frames;
 } pvt_policy;
 
 /* Set the launch policy for later count calls on this dag (drops a recorded

@@ -74,6 +74,29 @@ class Dag:
                                                _stream_handle(stream, self.device)))
         return out
 
+    def count_hist(self, begin=0, end=None, hist=None, kmax=None, stream=None):
+        """Add the (h, p) path counts of the roots begin <= r < end to hist
+        (int64 tensor [alpha+2, alpha+2], zeros if None) and return it: the
+        checkpointable state of a global count (pvt_count_hist)."""
+        kmax = self.alpha + 1 if kmax is None else int(kmax)
+        end = self.n if end is None else int(end)
+        H = self.alpha + 2
+        if hist is None:
+            hist = torch.zeros((H, H), dtype=torch.int64, device=self.device)
+        if hist.dtype != torch.int64 or tuple(hist.shape) != (H, H) or not hist.is_contiguous():
+            raise ValueError(f"hist must be a contiguous int64 tensor of shape {(H, H)}")
+        _lib.check(_lib.lib().pvt_count_hist(self._h, int(begin), end, kmax, ctypes.c_void_p(hist.data_ptr()),
+                                             _stream_handle(stream, self.device)))
+        return hist
+
+    def combine_hist(self, hist, kmax=None, W=None, out=None, stream=None):
+        """C_k words [kmax+1, W] from a path-count histogram (pvt_combine_hist)."""
+        kmax, W = self._args(kmax, W)
+        out = self._out(None, kmax, W, out)
+        _lib.check(_lib.lib().pvt_combine_hist(self._h, ctypes.c_void_p(hist.data_ptr()), kmax, W,
+                                               ctypes.c_void_p(out.data_ptr()), _stream_handle(stream, self.device)))
+        return out
+
     def count_local_vertex(self, kmax=None, W=None, out=None, stream=None):
         """c_k(v) as an int64 tensor [n, kmax+1, W]."""
         kmax, W = self._args(kmax, W)
@@ -92,7 +115,7 @@ class Dag:
         return out
 
     PHASES = ("peel", "orient", "walk_d32", "walk_d64", "walk_d128", "walk_d256", "walk_d512", "walk_d1024",
-              "finish")
+              "finish", "walk_frames")
 
     def stats(self):
         """Statistics of the last call on this dag (see pvt_stats): SCT walk
@@ -102,6 +125,7 @@ class Dag:
         _lib.check(_lib.lib().pvt_dag_stats(self._h, ctypes.byref(st)))
         return dict(sct_nodes=st.sct_nodes, sct_leaves=st.sct_leaves, pivot_words=st.pivot_words,
                     launches=st.launches, roots=list(st.roots), class_words=list(st.class_words),
+                    frame_words=st.frame_words, frames=st.frames,
                     ms=dict(zip(self.PHASES, list(st.ms))), peel_rounds=st.peel_rounds,
                     peel_levels=st.peel_levels)
 
@@ -109,18 +133,22 @@ class Dag:
         """The dag's launch policy (pvt_policy) as a dict."""
         pol = _lib.Policy()
         _lib.check(_lib.lib().pvt_dag_get_policy(self._h, ctypes.byref(pol)))
-        return dict(persistent=bool(pol.persistent), chunk=pol.chunk, split=list(pol.split), graph=bool(pol.graph))
+        return dict(persistent=bool(pol.persistent), chunk=pol.chunk, split=list(pol.split), graph=bool(pol.graph),
+                    frames=bool(pol.frames))
 
-    def set_policy(self, persistent: bool = True, chunk: int = 4, split=None, graph: bool = False):
+    def set_policy(self, persistent: bool = True, chunk: int = 4, split=None, graph: bool = False,
+                   frames: bool = True):
         """Launch policy of the walk kernels: persistent warps with a device
         work queue (default) or the plain one-warp-per-root form; per
         out-degree class whether heavy roots split across warps (7 flags,
-        default: every class above out-degree 32); and whether global counts
-        replay a recorded CUDA graph."""
+        default: every class above out-degree 32); whether global counts
+        replay a recorded CUDA graph; whether global counts walk the small
+        labels of the classes above 32 in a second, lighter kernel."""
         split = [0, 0, 1, 1, 1, 1, 1] if split is None else [int(x) for x in split]
         if len(split) != 7:
             raise ValueError("split needs one flag per out-degree class (7)")
-        pol = _lib.Policy(1 if persistent else 0, int(chunk), (ctypes.c_int32 * 7)(*split), 1 if graph else 0)
+        pol = _lib.Policy(1 if persistent else 0, int(chunk), (ctypes.c_int32 * 7)(*split), 1 if graph else 0,
+                          1 if frames else 0)
         _lib.check(_lib.lib().pvt_dag_set_policy(self._h, ctypes.byref(pol)))
 
     def autotune(self, kmax=None, W=None, out=None, stream=None):
@@ -135,7 +163,7 @@ class Dag:
                                                _stream_handle(stream, self.device), ctypes.byref(pol),
                                                ms.ctypes.data))
         return (dict(persistent=bool(pol.persistent), chunk=pol.chunk, split=list(pol.split),
-                     graph=bool(pol.graph)), ms, out)
+                     graph=bool(pol.graph), frames=bool(pol.frames)), ms, out)
 
     def set_profiling(self, on: bool):
         _lib.check(_lib.lib().pvt_dag_set_profiling(self._h, 1 if on else 0))

@@ -24,12 +24,13 @@ class Stats(ctypes.Structure):
     _fields_ = [("sct_nodes", ctypes.c_uint64), ("sct_leaves", ctypes.c_uint64),
                 ("pivot_words", ctypes.c_uint64), ("launches", ctypes.c_uint64),
                 ("roots", ctypes.c_uint64 * 7), ("class_words", ctypes.c_uint64 * 7),
-                ("ms", ctypes.c_float * 9), ("peel_rounds", ctypes.c_uint32), ("peel_levels", ctypes.c_uint32)]
+                ("frame_words", ctypes.c_uint64), ("frames", ctypes.c_uint64),
+                ("ms", ctypes.c_float * 10), ("peel_rounds", ctypes.c_uint32), ("peel_levels", ctypes.c_uint32)]
 
 class Policy(ctypes.Structure):
     """pvt_policy (include/pivoter.h)."""
     _fields_ = [("persistent", ctypes.c_int32), ("chunk", ctypes.c_int32), ("split", ctypes.c_int32 * 7),
-                ("graph", ctypes.c_int32)]
+                ("graph", ctypes.c_int32), ("frames", ctypes.c_int32)]
 
 
 class ServerConfig(ctypes.Structure):
@@ -41,7 +42,7 @@ class ServerConfig(ctypes.Structure):
 QUERY_GLOBAL, QUERY_VERTEX, QUERY_EDGE = 0, 1, 2
 
 # every symbol include/pivoter.h declares
-EXPORTS = ("pvt_orient", "pvt_dag_info", "pvt_dag_cores", "pvt_local_distribution", "pvt_count_global", "pvt_count_local_vertex",
+EXPORTS = ("pvt_orient", "pvt_dag_info", "pvt_dag_cores", "pvt_local_distribution", "pvt_count_hist", "pvt_combine_hist", "pvt_count_global", "pvt_count_local_vertex",
            "pvt_count_local_edge", "pvt_dag_stats", "pvt_dag_set_profiling", "pvt_dag_set_policy",
            "pvt_dag_get_policy", "pvt_dag_autotune",
            "pvt_count_global_noalloc", "pvt_server_create", "pvt_server_submit", "pvt_server_wait",
@@ -65,6 +66,10 @@ def load(path: str = LIB_PATH):
     lib.pvt_dag_info.restype = i32
     lib.pvt_dag_info.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(i32),
                                  ctypes.POINTER(i32)]
+    lib.pvt_count_hist.restype = i32
+    lib.pvt_count_hist.argtypes = [vp, i64, i64, i32, vp, vp]
+    lib.pvt_combine_hist.restype = i32
+    lib.pvt_combine_hist.argtypes = [vp, vp, i32, i32, vp, vp]
     lib.pvt_local_distribution.restype = i32
     lib.pvt_local_distribution.argtypes = [vp, i64, i32, i32, i32, vp, vp, ctypes.POINTER(i64), vp]
     lib.pvt_dag_cores.restype = i32

@@ -88,6 +88,7 @@ static void dag_release(pvt_dag *g)
         cudaFree(g->qready[c].p);
     }
     cudaFree(g->qctl);
+    cudaFree(g->cframes.p);
     for (int c = 0; c < NCLASS; ++c) cudaFree(g->gstack[c].p);
     cudaFree(g->d_stats);
     if (g->h_err) cudaFreeHost(g->h_err);
@@ -198,6 +199,17 @@ pvt_status pvt_count_local_edge(pvt_dag *dag, int32_t kmax, int32_t W, uint64_t 
     return count_local(dag, kmax, W, ce, true, (cudaStream_t)stream);
 }
 
+pvt_status pvt_count_hist(pvt_dag *dag, int64_t begin, int64_t end, int32_t kmax, uint64_t *hist, void *stream)
+{
+    return count_hist(dag, begin, end, kmax, hist, (cudaStream_t)stream);
+}
+
+pvt_status pvt_combine_hist(pvt_dag *dag, const uint64_t *hist, int32_t kmax, int32_t W, uint64_t *C,
+                            void *stream)
+{
+    return combine_hist(dag, hist, kmax, W, C, (cudaStream_t)stream);
+}
+
 pvt_status pvt_dag_stats(const pvt_dag *dag, pvt_stats *out)
 {
     if (!dag || !out) {
@@ -229,7 +241,8 @@ pvt_status pvt_dag_set_profiling(pvt_dag *dag, int32_t enable)
 pvt_status pvt_dag_set_policy(pvt_dag *dag, const pvt_policy *policy)
 {
     bool ok = dag && policy && (policy->persistent == 0 || policy->persistent == 1) && policy->chunk >= 1 &&
-              policy->chunk <= 32 && (policy->graph == 0 || policy->graph == 1);
+              policy->chunk <= 32 && (policy->graph == 0 || policy->graph == 1) &&
+              (policy->frames == 0 || policy->frames == 1);
     for (int c = 0; ok && c < NCLASS; ++c) ok = policy->split[c] == 0 || policy->split[c] == 1;
     if (!ok) {
         set_error("pvt_dag_set_policy: invalid argument");

@@ -157,9 +157,57 @@ static pvt_status ensure_binom(pvt_dag *g, int W, cudaStream_t s)
     return PVT_OK;
 }
 
-template <int MODE>
-static pvt_status launch_all(pvt_dag *g, const CountArgs &A, cudaStream_t s)
+// Second phase of a two-phase global count (k_walk_frames) on stream s.
+static pvt_status launch_frames(pvt_dag *g, const CountArgs &base, cudaStream_t s)
 {
+    CountArgs A = base;
+    A.cls = FRAMES_SLOT;
+    pvt_status st;
+    if ((st = grow(g->qframes[0], (size_t)SPLIT_QCAP * FRAME_WORDS, s)) != PVT_OK) return st;
+    if ((st = grow(g->qready[0], (size_t)SPLIT_QCAP * 2, s)) != PVT_OK) return st;
+    PVT_CK(cudaMemsetAsync(g->qready[0].p, 0, (size_t)SPLIT_QCAP * 2 * sizeof(uint32_t), s));
+    k_frames_init<<<1, 128, 0, s>>>(g->qctl, A.emit_count, A.emit_cap);
+    PVT_CK(cudaGetLastError());
+    A.qframes = g->qframes[0].p;
+    A.qready = g->qready[0].p;
+    A.qdone = g->qready[0].p + SPLIT_QCAP;
+    A.qctl = g->qctl;
+    A.qcap = SPLIT_QCAP;
+    constexpr size_t smem = sizeof(WarpWork<1>) * FRAME_WPB + sizeof(unsigned long long) * HIST_H * HIST_P;
+    auto kern = k_walk_frames<true>;
+    PVT_CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    PVT_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * FRAME_WPB, smem));
+    if (per_sm < 1) {
+        set_error("frame walk kernel cannot be resident");
+        return PVT_ECUDA;
+    }
+    phase_begin(g, PH_FRAMES, s);
+    kern<<<g->num_sms * per_sm, 32 * FRAME_WPB, smem, s>>>(A);
+    PVT_CK(cudaGetLastError());
+    phase_end(g, PH_FRAMES, s);
+    g->stats.launches += 2;
+    return PVT_OK;
+}
+
+template <int MODE>
+static pvt_status launch_all(pvt_dag *g, const CountArgs &A0, cudaStream_t s)
+{
+    // two-phase global counts: the classes above 32 emit their small labels
+    // as frames into cframes (capacity from the number of heavy roots; a
+    // full buffer only sends frames back to in-place walking)
+    CountArgs A = A0;
+    int64_t heavy = 0;
+    for (int c = 2; c < NCLASS; ++c) heavy += g->wcnt[c];
+    const bool frames = MODE == MODE_GLOBAL && g->policy.frames && g->policy.persistent && heavy > 0;
+    if (frames) {
+        const unsigned cap = (unsigned)std::min<int64_t>(std::max<int64_t>(64 * heavy, 1 << 16), 1 << 22);
+        pvt_status st = grow(g->cframes, (size_t)cap * FRAME_WORDS, s);
+        if (st != PVT_OK) return st;
+        A.emit = g->cframes.p;
+        A.emit_count = g->d_q + 8;
+        A.emit_cap = cap;
+    }
     // heavy classes on side streams so that they overlap the light ones (or
     // all on s, one after another, when the autotuner times them)
     const bool serial = g->serial;
@@ -169,7 +217,7 @@ static pvt_status launch_all(pvt_dag *g, const CountArgs &A, cudaStream_t s)
         cudaStream_t cs = serial ? s : g->side[c];
         if (!serial) PVT_CK(cudaStreamWaitEvent(cs, g->ev_fork, 0));
         switch (c) {
-            case 1: st = launch_class<1, MODE, MODE == MODE_GLOBAL>(g, A, c, cs); break;
+            case 1: st = launch_class<1, MODE, MODE == MODE_GLOBAL>(g, A0, c, cs); break;
             case 2: st = launch_class<2, MODE, MODE == MODE_GLOBAL>(g, A, c, cs); break;
             case 3: st = launch_class<4, MODE, MODE == MODE_GLOBAL>(g, A, c, cs); break;
             case 4: st = launch_class<8, MODE, MODE == MODE_GLOBAL>(g, A, c, cs); break;
@@ -177,6 +225,14 @@ static pvt_status launch_all(pvt_dag *g, const CountArgs &A, cudaStream_t s)
             case 6: st = launch_class<32, MODE, MODE == MODE_GLOBAL>(g, A, c, cs); break;
         }
         if (!serial) PVT_CK(cudaEventRecord(g->ev_join[c], cs));
+    }
+    if (st != PVT_OK) return st;
+    if (frames) {
+        // the frame walk follows the heavy classes; the <= 32 class may
+        // still be running beside it
+        if (!serial)
+            for (int c = NCLASS - 1; c >= 2; --c) PVT_CK(cudaStreamWaitEvent(s, g->ev_join[c], 0));
+        if ((st = launch_frames(g, A, s)) != PVT_OK) return st;
     }
     if (!serial)
         for (int c = NCLASS - 1; c >= 1; --c) PVT_CK(cudaStreamWaitEvent(s, g->ev_join[c], 0));
@@ -186,19 +242,27 @@ static pvt_status launch_all(pvt_dag *g, const CountArgs &A, cudaStream_t s)
 static void begin_call(pvt_dag *g)
 {
     stats_reset(g);
+    // walk every root unless a range call narrows the set
+    g->wroots = g->roots;
+    for (int c = 0; c < NCLASS; ++c) {
+        g->wstart[c] = g->class_start[c];
+        g->wcnt[c] = g->class_cnt[c];
+    }
     for (int c = 0; c < NCLASS; ++c) g->stats.roots[c] = (uint64_t)g->class_cnt[c];
 }
 
 // Copy the walk statistics back, synchronise and check the device status.
 static pvt_status end_call(pvt_dag *g, cudaStream_t s, const char *fn)
 {
-    PVT_CK(cudaMemcpyAsync(g->h_stats, g->d_stats, (3 + NCLASS) * sizeof(unsigned long long),
+    PVT_CK(cudaMemcpyAsync(g->h_stats, g->d_stats, (3 + NCLASS + 2) * sizeof(unsigned long long),
                            cudaMemcpyDeviceToHost, s));
     pvt_status st = check_device(g, s, fn);
     g->stats.sct_nodes = g->h_stats[0];
     g->stats.sct_leaves = g->h_stats[1];
     g->stats.pivot_words = g->h_stats[2];
     for (int c = 0; c < NCLASS; ++c) g->stats.class_words[c] = g->h_stats[3 + c];
+    g->stats.frame_words = g->h_stats[3 + FRAMES_SLOT];
+    g->stats.frames = g->h_stats[3 + FRAMES_SLOT + 1];
     return st;
 }
 
@@ -250,11 +314,11 @@ static pvt_status enqueue_global(pvt_dag *g, int32_t kmax, int32_t W, uint64_t *
     A.err = g->d_err;
     A.stats = g->d_stats;
     if ((st = launch_all<MODE_GLOBAL>(g, A, s)) != PVT_OK) return st;
-    phase_begin(g, NPHASE - 1, s);
+    phase_begin(g, PH_FINISH, s);
     k_combine<<<kmax + 1, 256, 0, s>>>(g->hist.p, hstride, g->binom.p, W, kmax,
                                        reinterpret_cast<unsigned long long *>(C), g->d_err);
     PVT_CK(cudaGetLastError());
-    phase_end(g, NPHASE - 1, s);
+    phase_end(g, PH_FINISH, s);
     g->stats.launches++;
     return PVT_OK;
 }
@@ -325,6 +389,120 @@ pvt_status count_global(pvt_dag *g, int32_t kmax, int32_t W, uint64_t *C, cudaSt
     return use_graph ? record_graph(g, kmax, W, C) : PVT_OK;
 }
 
+// ------------------------------------------- root ranges and checkpoints
+
+struct ClassBounds {
+    int64_t start[NCLASS], cnt[NCLASS];
+};
+
+__global__ void k_range_flags(const uint32_t *__restrict__ roots, int64_t n, int64_t begin, int64_t end,
+                              uint32_t *flag)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        flag[i] = roots[i] >= (uint64_t)begin && roots[i] < (uint64_t)end;
+}
+
+__global__ void k_range_scatter(const uint32_t *__restrict__ roots, int64_t n, const uint32_t *__restrict__ flag,
+                                const int64_t *__restrict__ pos, uint32_t *out)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        if (flag[i]) out[pos[i]] = roots[i];
+}
+
+// Start and length of each class inside the compacted range.
+__global__ void k_range_bounds(const int64_t *__restrict__ pos, ClassBounds full, int64_t *out)
+{
+    const int c = threadIdx.x;
+    if (c < NCLASS) {
+        const int64_t a = pos[full.start[c]], b = pos[full.start[c] + full.cnt[c]];
+        out[c] = a;
+        out[NCLASS + c] = b - a;
+    }
+}
+
+pvt_status count_hist(pvt_dag *g, int64_t begin, int64_t end, int32_t kmax, uint64_t *hist, cudaStream_t s)
+{
+    if (!g || !hist || kmax < 0 || begin < 0 || end < begin) {
+        set_error("pvt_count_hist: invalid argument");
+        return PVT_EINVAL;
+    }
+    begin_call(g);
+    const int64_t n = g->n;
+    end = std::min(end, n);
+    begin = std::min(begin, end);
+    pvt_status st;
+    if (n > 0) {
+        // the range's roots, class by class in the order of g->roots
+        if ((st = grow(g->range_roots, (size_t)2 * n, s)) != PVT_OK) return st;
+        if ((st = grow(g->range_pos, (size_t)n + 1, s)) != PVT_OK) return st;
+        uint32_t *flag = g->range_roots.p, *out = g->range_roots.p + n;
+        const int grid = g->num_sms * 4;
+        k_range_flags<<<grid, 256, 0, s>>>(g->roots, n, begin, end, flag);
+        PVT_CK(cudaGetLastError());
+        if ((st = exclusive_scan_u32_i64(flag, g->range_pos.p, n, s)) != PVT_OK) return st;
+        k_range_scatter<<<grid, 256, 0, s>>>(g->roots, n, flag, g->range_pos.p, out);
+        ClassBounds full{};
+        for (int c = 0; c < NCLASS; ++c) {
+            full.start[c] = g->class_start[c];
+            full.cnt[c] = g->class_cnt[c];
+        }
+        int64_t *d_b = reinterpret_cast<int64_t *>(flag);  // flags are spent; reuse their words
+        k_range_bounds<<<1, 32, 0, s>>>(g->range_pos.p, full, d_b);
+        PVT_CK(cudaGetLastError());
+        int64_t hb[2 * NCLASS];
+        PVT_CK(cudaMemcpyAsync(hb, d_b, sizeof(hb), cudaMemcpyDeviceToHost, s));
+        PVT_CK(cudaStreamSynchronize(s));
+        g->wroots = out;
+        for (int c = 0; c < NCLASS; ++c) {
+            g->wstart[c] = hb[c];
+            g->wcnt[c] = hb[NCLASS + c];
+            g->stats.roots[c] = (uint64_t)hb[NCLASS + c];
+        }
+        g->stats.launches += 7;
+    }
+    const int hstride = g->alpha + 2;
+    PVT_CK(cudaMemsetAsync(g->d_err, 0, sizeof(unsigned), s));
+    PVT_CK(cudaMemsetAsync(g->d_q, 0, 16 * sizeof(unsigned), s));
+    PVT_CK(cudaMemsetAsync(g->d_stats, 0, 16 * sizeof(unsigned long long), s));
+    if (g->wcnt[0] && kmax >= 1) {
+        k_add_leaf<<<1, 32, 0, s>>>(reinterpret_cast<unsigned long long *>(hist) + hstride,
+                                    (unsigned long long)g->wcnt[0]);
+        PVT_CK(cudaGetLastError());
+        g->stats.launches++;
+    }
+    CountArgs A{};
+    A.orow = g->orow;
+    A.ocol = g->ocol;
+    A.hist = reinterpret_cast<unsigned long long *>(hist);
+    A.hstride = hstride;
+    A.W = 1;
+    A.Bw = 1;
+    A.kmax = kmax;
+    A.err = g->d_err;
+    A.stats = g->d_stats;
+    if ((st = launch_all<MODE_GLOBAL>(g, A, s)) != PVT_OK) return st;
+    return end_call(g, s, "pvt_count_hist");
+}
+
+pvt_status combine_hist(pvt_dag *g, const uint64_t *hist, int32_t kmax, int32_t W, uint64_t *C, cudaStream_t s)
+{
+    pvt_status st = check_args(g, kmax, W, C, 1, "pvt_combine_hist");
+    if (st != PVT_OK) return st;
+    if (!hist) {
+        set_error("pvt_combine_hist: invalid argument");
+        return PVT_EINVAL;
+    }
+    begin_call(g);
+    if ((st = ensure_binom(g, W, s)) != PVT_OK) return st;
+    PVT_CK(cudaMemsetAsync(g->d_err, 0, sizeof(unsigned), s));
+    PVT_CK(cudaMemsetAsync(g->d_stats, 0, 16 * sizeof(unsigned long long), s));
+    k_combine<<<kmax + 1, 256, 0, s>>>(reinterpret_cast<const unsigned long long *>(hist), g->alpha + 2, g->binom.p,
+                                       W, kmax, reinterpret_cast<unsigned long long *>(C), g->d_err);
+    PVT_CK(cudaGetLastError());
+    g->stats.launches++;
+    return end_call(g, s, "pvt_combine_hist");
+}
+
 // Per-class minimum over three candidate policies, classes timed one at a time.
 pvt_status autotune(pvt_dag *g, int32_t kmax, int32_t W, uint64_t *C, cudaStream_t s, pvt_policy *chosen,
                     float *ms)
@@ -334,9 +512,9 @@ pvt_status autotune(pvt_dag *g, int32_t kmax, int32_t W, uint64_t *C, cudaStream
         return PVT_EINVAL;
     }
     static const pvt_policy cand[3] = {
-        {1, 4, {0, 0, 1, 1, 1, 1, 1}, 0},
-        {1, 1, {0, 0, 0, 0, 0, 0, 0}, 0},
-        {1, 16, {0, 0, 1, 1, 1, 1, 1}, 0},
+        {1, 4, {0, 0, 1, 1, 1, 1, 1}, 0, 1},
+        {1, 1, {0, 0, 0, 0, 0, 0, 0}, 0, 1},
+        {1, 16, {0, 0, 1, 1, 1, 1, 1}, 0, 1},
     };
     const pvt_policy saved = g->policy;
     const bool saved_prof = g->profiling;

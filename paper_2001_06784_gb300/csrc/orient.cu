@@ -530,6 +530,7 @@ __global__ void k_outdeg(int64_t n, const int64_t *__restrict__ rp, const uint32
     const int lane = threadIdx.x & 31;
     const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    unsigned most = 0;  // largest out-degree this warp has seen
     for (int64_t v = warp; v < n; v += nwarps) {
         uint32_t rv = rnd[v];
         unsigned c = 0;
@@ -537,12 +538,11 @@ __global__ void k_outdeg(int64_t n, const int64_t *__restrict__ rp, const uint32
             uint32_t u = col[j];
             c += key_less(rv, (uint32_t)v, rnd[u], u);
         }
-        for (int o = 16; o; o >>= 1) c += __shfl_xor_sync(FULL, c, o);
-        if (lane == 0) {
-            odeg[v] = c;
-            atomicMax(alpha, c);
-        }
+        c = __reduce_add_sync(FULL, c);
+        if (lane == 0) odeg[v] = c;
+        most = max(most, c);
     }
+    if (lane == 0 && most) atomicMax(alpha, most);
 }
 
 // Out-lists in CSR order (ascending id), compacted with a warp ballot.
@@ -581,21 +581,41 @@ __host__ __device__ inline int degree_class(uint32_t d)
     return c;
 }
 
-__global__ void k_deg_hist(int64_t n, const uint32_t *__restrict__ odeg, unsigned *hist)
+// (a block-shared histogram first: out-degrees crowd into a few small values)
+__global__ void k_deg_hist(int64_t n, const uint32_t *__restrict__ odeg, unsigned *hist, int nd)
 {
+    extern __shared__ unsigned sh[];
+    for (int i = threadIdx.x; i < nd; i += blockDim.x) sh[i] = 0;
+    __syncthreads();
     for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
          v += (int64_t)gridDim.x * blockDim.x)
-        atomicAdd(&hist[odeg[v]], 1u);
+        atomicAdd(&sh[min(odeg[v], (uint32_t)(nd - 1))], 1u);
+    __syncthreads();
+    for (int i = threadIdx.x; i < nd; i += blockDim.x)
+        if (sh[i]) atomicAdd(&hist[i], sh[i]);
 }
 
 // Scatter roots so that out-degrees descend within the array (slot[d] holds
-// the next free position for out-degree d).
+// the next free position for out-degree d); lanes with equal out-degrees
+// share one atomic.
 __global__ void k_deg_scatter(int64_t n, const uint32_t *__restrict__ odeg, unsigned *slot,
                               uint32_t *roots)
 {
-    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
-         v += (int64_t)gridDim.x * blockDim.x)
-        roots[atomicAdd(&slot[odeg[v]], 1u)] = (uint32_t)v;
+    const int lane = threadIdx.x & 31;
+    for (int64_t base = blockIdx.x * (int64_t)blockDim.x + threadIdx.x - lane; base < n;
+         base += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t v = base + lane;
+        const bool valid = v < n;
+        const unsigned act = __ballot_sync(FULL, valid);
+        if (!valid) continue;
+        const uint32_t d = odeg[v];
+        const unsigned peers = __match_any_sync(act, d);
+        const int leader = __ffs(peers) - 1;
+        unsigned at = 0;
+        if (lane == leader) at = atomicAdd(&slot[d], (unsigned)__popc(peers));
+        at = __shfl_sync(peers, at, leader);
+        roots[at + __popc(peers & ((1u << lane) - 1u))] = (uint32_t)v;
+    }
 }
 
 // ------------------------------------------------------------------ scan
@@ -860,7 +880,7 @@ pvt_status orient_build(pvt_dag *g, uint32_t flags, cudaStream_t s)
     const int nd = g->alpha + 1;
     PVT_CK(cudaMallocAsync(&dhist, (size_t)nd * sizeof(unsigned), s));
     PVT_CK(cudaMemsetAsync(dhist, 0, (size_t)nd * sizeof(unsigned), s));
-    k_deg_hist<<<grid, 256, 0, s>>>(n, odeg, dhist);
+    k_deg_hist<<<grid, 256, (size_t)nd * sizeof(unsigned), s>>>(n, odeg, dhist, nd);
     g->stats.launches++;
     std::vector<unsigned> hh(nd), slot(nd);
     PVT_CK(cudaMemcpyAsync(hh.data(), dhist, (size_t)nd * sizeof(unsigned), cudaMemcpyDeviceToHost, s));

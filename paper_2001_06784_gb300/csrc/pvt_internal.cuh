@@ -18,7 +18,8 @@ constexpr uint32_t NOT_REMOVED = 0xFFFFFFFFu;
 constexpr int NCLASS = 7;              // d = 0, <=32, <=64, <=128, <=256, <=512, <=1024
 constexpr int MAX_ALPHA = 1024;        // largest degeneracy (out-degree) supported
 constexpr int BATCH_MAX_ALPHA = 512;   // largest degeneracy of a served (batched) graph
-constexpr int NPHASE = NCLASS + 2;     // peel, orient, one walk per class >= 1, finish
+constexpr int NPHASE = NCLASS + 3;     // peel, orient, one walk per class >= 1, finish, frame walk
+constexpr int PH_FINISH = NCLASS + 1, PH_FRAMES = NCLASS + 2;
 constexpr int WMAX = 20;               // largest W (64-bit words per count) supported
 
 // Device-side error bits (one 32-bit status word per dag).
@@ -55,6 +56,12 @@ struct pvt_dag {
     uint32_t *roots = nullptr;     // roots grouped by class, descending out-degree
     int64_t class_start[pvt::NCLASS] = {0};  // first position of each class in roots
     int64_t class_cnt[pvt::NCLASS] = {0};
+    // the roots a count walks: every root (wroots = roots) or a range of them
+    // (pvt_count_hist), grouped by class the same way
+    const uint32_t *wroots = nullptr;
+    int64_t wstart[pvt::NCLASS] = {0}, wcnt[pvt::NCLASS] = {0};
+    pvt::DevBuf<uint32_t> range_roots;  // roots of the last range, and its scan
+    pvt::DevBuf<int64_t> range_pos;
     unsigned *d_err = nullptr;     // device status word
     unsigned *d_q = nullptr;       // work-queue heads [16]
     unsigned *h_err = nullptr;     // pinned host copy of the status word
@@ -72,7 +79,8 @@ struct pvt_dag {
     unsigned long long *h_stats = nullptr;  // pinned host copy
     pvt_stats stats = {};
     bool profiling = false;
-    pvt_policy policy = {1, 4, {0, 0, 1, 1, 1, 1, 1}, 0};
+    pvt_policy policy = {1, 4, {0, 0, 1, 1, 1, 1, 1}, 0, 1};
+    pvt::DevBuf<uint32_t> cframes;  // compacted frames emitted by the wide walks
     bool serial = false;           // launch the classes one after another on the caller's stream
     bool capturing = false;        // recording a CUDA graph: no phase events
     cudaGraphExec_t graph_exec = nullptr;  // recorded global count (policy.graph)
@@ -150,6 +158,8 @@ pvt_status count_local(pvt_dag *g, int32_t kmax, int32_t W, uint64_t *out, bool 
                        cudaStream_t s);
 pvt_status autotune(pvt_dag *g, int32_t kmax, int32_t W, uint64_t *C, cudaStream_t s, pvt_policy *chosen,
                     float *ms);
+pvt_status count_hist(pvt_dag *g, int64_t begin, int64_t end, int32_t kmax, uint64_t *hist, cudaStream_t s);
+pvt_status combine_hist(pvt_dag *g, const uint64_t *hist, int32_t kmax, int32_t W, uint64_t *C, cudaStream_t s);
 void drop_graph(pvt_dag *g);
 
 // Exclusive prefix sum of uint32 counts into int64 offsets (out has n+1 entries).

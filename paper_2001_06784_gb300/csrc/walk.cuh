@@ -141,6 +141,11 @@ struct CountArgs {
     uint32_t *qctl;             // counters, each on its own 128-byte line (Q_* offsets)
     unsigned qcap;              // power of two
     uint32_t *gstack;           // wide classes: per-warp DFS stacks, (32*NW+1)*NW words each
+    // two-phase global counts: the wide walk emits every compacted subtree
+    // as a frame (layout below) for k_walk_frames; null: walk them in place
+    uint32_t *emit;             // [emit_cap][FRAME_WORDS]
+    unsigned *emit_count;       // frames reserved so far (may pass emit_cap)
+    unsigned emit_cap;
 };
 
 // Work queue of a split launch, a ring of qcap slots.  Idle warps take a
@@ -151,7 +156,8 @@ struct CountArgs {
 // no item is outstanding: then no warp can produce another frame.
 constexpr int Q_HEAD = 0, Q_TAIL = 32, Q_OUT = 64, Q_ROOT = 96, QCTL_WORDS = 128;
 // Frame: [0] kind; wide (1): [1] root index, [2] d, [3] (h<<16)|p, [4..4+NW) S;
-// compacted (2): [1] (h<<16)|p, [2] S, [4..36) the 32 one-word rows.
+// compacted (2): [1] (h<<16)|p, [2] S, [3] out-degree class of the root,
+// [4..36) the 32 one-word rows.
 constexpr int FRAME_WORDS = 36;
 constexpr uint32_t FRAME_WIDE = 1u, FRAME_COMPACT = 2u;
 
@@ -390,11 +396,11 @@ struct Outer {
 };
 
 // Donation clock of one warp, shared by the wide and the compacted walks:
-// the queue is consulted once every DONATE_EVERY nodes.
+// the queue is consulted once every `every` nodes.
 struct Clock {
     unsigned nodes = 0, next = 0;
+    unsigned every = 16;  // nodes between looks at the queue
 };
-constexpr unsigned DONATE_EVERY = 16;
 
 // Hand wide frame f (of root qi, out-degree d) to the frame queue.
 template <int NW>
@@ -486,7 +492,7 @@ __device__ void compact_loop(WarpWork<NW> &Wk, unsigned long long *shist, const 
                     top += nR;
                     __syncwarp();
                     if (SPLIT && clk.nodes >= clk.next) {
-                        clk.next = clk.nodes + DONATE_EVERY;
+                        clk.next = clk.nodes + clk.every;
                         // waiting warps get the largest pending work first: the
                         // enclosing wide walk's oldest frame, else our oldest
                         int ndon = 0, wide = 0;
@@ -513,6 +519,7 @@ __device__ void compact_loop(WarpWork<NW> &Wk, unsigned long long *shist, const 
                                     fr[0] = FRAME_COMPACT;
                                     fr[1] = Wk.hp1[bot];
                                     fr[2] = Wk.stk1[bot];
+                                    fr[3] = (uint32_t)A.cls;
                                 }
                                 frame_publish(A, lane, t);
                                 bot += 1;
@@ -548,10 +555,8 @@ __device__ void compact_loop(WarpWork<NW> &Wk, unsigned long long *shist, const 
 // has s <= 32 members: relabel them 0..s-1 in ascending order; lane k gets
 // row k of the induced adjacency -- by symmetry, the ballot over lanes j of
 // "member k is in my row" is exactly that row.
-template <int NW, bool SHIST, bool SPLIT>
-__device__ void walk_compact(WarpWork<NW> &Wk, unsigned long long *shist, const CountArgs &A, int lane,
-                             const uint32_t *S, int s, int h, int p, WalkCounters &wc, const Outer *outer,
-                             Clock &clk)
+template <int NW>
+__device__ __forceinline__ uint32_t compact_rows(WarpWork<NW> &Wk, int lane, const uint32_t *S, int s)
 {
     constexpr int RS = WarpWork<NW>::RS;
     int before = 0;
@@ -570,8 +575,35 @@ __device__ void walk_compact(WarpWork<NW> &Wk, unsigned long long *shist, const 
         if (lane == k) r1 = col;
     }
     __syncwarp();
-    compact_loop<NW, SHIST, SPLIT>(Wk, shist, A, lane, r1, s >= 32 ? FULL : ((1u << s) - 1u), h, p, wc, outer,
-                                   clk);
+    return r1;
+}
+
+// Walk the compacted subtree in place, or (two-phase global counts) emit it
+// as a frame for k_walk_frames while the buffer has room.
+template <int NW, bool SHIST, bool SPLIT>
+__device__ void walk_compact(WarpWork<NW> &Wk, unsigned long long *shist, const CountArgs &A, int lane,
+                             const uint32_t *S, int s, int h, int p, WalkCounters &wc, const Outer *outer,
+                             Clock &clk)
+{
+    const uint32_t r1 = compact_rows<NW>(Wk, lane, S, s);
+    const uint32_t S1 = s >= 32 ? FULL : ((1u << s) - 1u);
+    if (A.emit) {
+        unsigned i = 0;
+        if (lane == 0) i = atomicAdd(A.emit_count, 1u);
+        i = __shfl_sync(FULL, i, 0);
+        if (i < A.emit_cap) {
+            uint32_t *fr = A.emit + (size_t)i * FRAME_WORDS;
+            fr[4 + lane] = r1;
+            if (lane == 0) {
+                fr[0] = FRAME_COMPACT;
+                fr[1] = ((uint32_t)h << 16) | (uint32_t)p;
+                fr[2] = S1;
+                fr[3] = (uint32_t)A.cls;
+            }
+            return;
+        }
+    }
+    compact_loop<NW, SHIST, SPLIT>(Wk, shist, A, lane, r1, S1, h, p, wc, outer, clk);
 }
 
 // One walk item: a whole root r (frame == nullptr), or a frame of root qi's
@@ -804,7 +836,7 @@ __device__ void walk_root(WarpWork<NW> &Wk, unsigned long long *shist, const Cou
                     top += before;
                     __syncwarp();  // pushed frames visible to every lane
                     if (SPLIT && clk.nodes >= clk.next) {
-                        clk.next = clk.nodes + DONATE_EVERY;
+                        clk.next = clk.nodes + clk.every;
                         // donate the oldest pending frame (largest subtree) to an idle warp
                         int ndon = 0;
                         if (lane == 0 && top - bot >= 2) {
@@ -880,6 +912,47 @@ __device__ __forceinline__ void bind_warp(WarpWork<NW> &Wk, unsigned char *local
     if (WarpWork<NW>::GSTACK) Wk.gstk = gstack + (size_t)warp_global * (32 * NW + 1) * NW;
 }
 
+// Lane 0 of a split launch: the next item -- 2 with v = a fresh item index
+// below nitems, 1 with v = the ticket of a donated frame, 3 when no work is
+// left (or an error or a timeout ended the launch).
+__device__ __forceinline__ int queue_take(const CountArgs &A, unsigned nitems, unsigned &v)
+{
+    if (vload(A.qctl + Q_ROOT) < nitems) {
+        const unsigned rr = atomicAdd(A.qctl + Q_ROOT, 1u);
+        if (rr < nitems) { v = rr; return 2; }
+    }
+    // a ticket for the next donated frame; wait on its own slot
+    int kind = 0;
+    const unsigned t = atomicAdd(A.qctl + Q_HEAD, 1u);
+    unsigned last_out = 0xFFFFFFFFu, nap = 64;
+    unsigned long long t0 = global_ns();
+    const unsigned slot = t & (A.qcap - 1u);
+    for (;;) {
+        if (vload(A.qready + slot) == t + 1u) { kind = 1; v = t; break; }
+        const unsigned out = vload(A.qctl + Q_OUT);
+        if (out == 0 || (vload(A.err) & (DERR_STACK | DERR_RANGE | DERR_TIMEOUT))) { kind = 3; break; }
+        if (out != last_out) { last_out = out; t0 = global_ns(); }
+        else if (global_ns() - t0 > SPLIT_IDLE_LIMIT_NS) { atomicOr(A.err, DERR_TIMEOUT); kind = 3; break; }
+        __nanosleep(nap);
+        nap = min(nap * 2u, 2048u);
+    }
+    if (kind == 1) __threadfence();
+    return kind;
+}
+
+// Copy donated frame t out of the ring into fb and release its slot.
+__device__ __forceinline__ void frame_take(const CountArgs &A, int lane, unsigned t, uint32_t *fb)
+{
+    const uint32_t *fr = A.qframes + (size_t)(t & (A.qcap - 1u)) * FRAME_WORDS;
+    fb[lane] = __ldcg(fr + lane);
+    if (lane < FRAME_WORDS - 32) fb[32 + lane] = __ldcg(fr + 32 + lane);
+    __syncwarp();
+    if (lane == 0) {
+        __threadfence();
+        atomicExch(A.qdone + (t & (A.qcap - 1u)), t + 1u);
+    }
+}
+
 template <int NW, int MODE, bool SHIST, bool PERSIST, bool SPLIT>
 __global__ void __launch_bounds__(32 * warps_per_block<NW>())
     k_count(CountArgs A)
@@ -903,45 +976,15 @@ __global__ void __launch_bounds__(32 * warps_per_block<NW>())
     if (SPLIT) {
         // heavy roots and donated subtree frames from one device work queue
         for (;;) {
-            int kind = 0;  // 1: donated frame in slot v, 2: fresh root v, 3: no more work
             unsigned v = 0;
-            if (lane == 0) {
-                if (vload(A.qctl + Q_ROOT) < A.nroots) {
-                    const unsigned rr = atomicAdd(A.qctl + Q_ROOT, 1u);
-                    if (rr < A.nroots) { kind = 2; v = rr; }
-                }
-                if (kind == 0) {
-                    // a ticket for the next donated frame; wait on its own slot
-                    const unsigned t = atomicAdd(A.qctl + Q_HEAD, 1u);
-                    unsigned last_out = 0xFFFFFFFFu, nap = 64;
-                    unsigned long long t0 = global_ns();
-                    const unsigned slot = t & (A.qcap - 1u);
-                    for (;;) {
-                        if (vload(A.qready + slot) == t + 1u) { kind = 1; v = t; break; }
-                        const unsigned out = vload(A.qctl + Q_OUT);
-                        if (out == 0 || (vload(A.err) & (DERR_STACK | DERR_RANGE | DERR_TIMEOUT))) { kind = 3; break; }
-                        if (out != last_out) { last_out = out; t0 = global_ns(); }
-                        else if (global_ns() - t0 > SPLIT_IDLE_LIMIT_NS) { atomicOr(A.err, DERR_TIMEOUT); kind = 3; break; }
-                        __nanosleep(nap);
-                        nap = min(nap * 2u, 2048u);
-                    }
-                    if (kind == 1) __threadfence();
-                }
-            }
+            int kind = lane == 0 ? queue_take(A, A.nroots, v) : 0;
             kind = __shfl_sync(FULL, kind, 0);
             v = __shfl_sync(FULL, v, 0);
             if (kind == 3) break;
             if (kind == 1) {
                 // copy the frame out and release its ring slot at once
-                const uint32_t *fr = A.qframes + (size_t)(v & (A.qcap - 1u)) * FRAME_WORDS;
                 uint32_t *fb = ww[wid].fbuf;
-                fb[lane] = __ldcg(fr + lane);
-                if (lane < FRAME_WORDS - 32) fb[32 + lane] = __ldcg(fr + 32 + lane);
-                __syncwarp();
-                if (lane == 0) {
-                    __threadfence();
-                    atomicExch(A.qdone + (v & (A.qcap - 1u)), v + 1u);
-                }
+                frame_take(A, lane, v, fb);
                 if (fb[0] == FRAME_COMPACT) {
                     const uint32_t hp0 = fb[1];
                     Clock clk;
@@ -1009,10 +1052,10 @@ constexpr unsigned SPLIT_QCAP = 1u << 17;
 template <int NW, int MODE, bool SHIST>
 pvt_status launch_class(pvt_dag *g, const CountArgs &base, int cls, cudaStream_t s)
 {
-    const unsigned cnt = (unsigned)g->class_cnt[cls];
+    const unsigned cnt = (unsigned)g->wcnt[cls];
     if (cnt == 0) return PVT_OK;
     CountArgs A = base;
-    A.roots = g->roots + g->class_start[cls];
+    A.roots = g->wroots + g->wstart[cls];
     A.nroots = cnt;
     A.qhead = g->d_q + cls;
     A.cls = cls;
@@ -1069,6 +1112,95 @@ pvt_status launch_class(pvt_dag *g, const CountArgs &base, int cls, cudaStream_t
     phase_end(g, 1 + cls, s);
     g->stats.launches++;
     return PVT_OK;
+}
+
+// ------------------------------------------------- compacted-frame walk
+//
+// Second phase of a two-phase global count: every compacted subtree that
+// the wide walks of the classes above 32 emitted, walked in one-word bitsets
+// (compact_loop).  The per-warp state is small (compact stack, frame copy),
+// so far more warps stay resident than in the wide kernels, whose shared
+// adjacency rows limit them; idle warps take donated compacted frames from a
+// ring queue exactly as in the split form.  Words go to stats slot
+// 3 + FRAMES_SLOT, the emitted frame count to stats[3 + FRAMES_SLOT + 1].
+constexpr int FRAME_WPB = 8;
+constexpr int FRAMES_SLOT = NCLASS;
+constexpr unsigned FRAMES_CHUNK = 4;
+
+template <bool SHIST>
+__global__ void __launch_bounds__(32 * FRAME_WPB) k_walk_frames(CountArgs A)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    WarpWork<1> *ww = reinterpret_cast<WarpWork<1> *>(smem);
+    unsigned long long *shist = reinterpret_cast<unsigned long long *>(ww + FRAME_WPB);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const unsigned emitted = *(volatile unsigned *)A.emit_count;
+    const unsigned nframes = min(emitted, A.emit_cap);
+    if (blockIdx.x == 0 && threadIdx.x == 0) A.stats[3 + FRAMES_SLOT + 1] = emitted;
+    WalkCounters wc;
+    if (SHIST) {
+        for (int i = threadIdx.x; i < HIST_H * HIST_P; i += blockDim.x) shist[i] = 0;
+        __syncthreads();
+    }
+    unsigned cur = 0, end = 0;  // lane 0: claimed emitted frames [cur, end)
+    for (;;) {
+        unsigned v = 0;
+        int kind = 0;
+        if (lane == 0) {
+            if (cur < end) {
+                kind = 2;
+                v = cur++;
+            } else if (vload(A.qctl + Q_ROOT) < nframes) {
+                // FRAMES_CHUNK emitted frames per claim, prefetched into L2
+                // (the buffer outgrows L2 once the wide walks are done)
+                const unsigned rr = atomicAdd(A.qctl + Q_ROOT, FRAMES_CHUNK);
+                if (rr < nframes) {
+                    kind = 2;
+                    v = rr;
+                    cur = rr + 1;
+                    end = min(rr + FRAMES_CHUNK, nframes);
+                    const char *a = reinterpret_cast<const char *>(A.emit + (size_t)rr * FRAME_WORDS);
+                    const char *b = reinterpret_cast<const char *>(A.emit + (size_t)end * FRAME_WORDS);
+                    for (; a < b; a += 128) asm volatile("prefetch.global.L2 [%0];" ::"l"(a));
+                }
+            }
+            if (kind == 0) kind = queue_take(A, 0u, v);
+        }
+        kind = __shfl_sync(FULL, kind, 0);
+        v = __shfl_sync(FULL, v, 0);
+        if (kind == 3) break;
+        const uint32_t *fr;
+        if (kind == 1) {
+            frame_take(A, lane, v, ww[wid].fbuf);
+            fr = ww[wid].fbuf;
+        } else {
+            fr = A.emit + (size_t)v * FRAME_WORDS;
+        }
+        const uint32_t r1 = fr[4 + lane], S1 = fr[2], hp0 = fr[1];
+        Clock clk;
+        clk.every = 64;
+        compact_loop<1, SHIST, true>(ww[wid], shist, A, lane, r1, S1, (int)(hp0 >> 16), (int)(hp0 & 0xFFFFu), wc,
+                                     nullptr, clk);
+        wc.fold();
+        __syncwarp();
+        if (lane == 0) atomicSub(A.qctl + Q_OUT, 1u);
+    }
+    wc.flush(A.stats, FRAMES_SLOT, lane);
+    if (SHIST) {
+        __syncthreads();
+        for (int i = threadIdx.x; i < HIST_H * HIST_P; i += blockDim.x) {
+            unsigned long long x = shist[i];
+            if (x) atomicAdd(&A.hist[(size_t)(i / HIST_P) * A.hstride + (i % HIST_P)], x);
+        }
+    }
+}
+
+// Queue counters of the frame walk: outstanding items = the emitted frames
+// (read on the device: the count is final once the wide walks are done).
+static __global__ void k_frames_init(uint32_t *qctl, const unsigned *emit_count, unsigned cap)
+{
+    for (int i = threadIdx.x; i < QCTL_WORDS; i += blockDim.x)
+        qctl[i] = i == Q_OUT ? min(*emit_count, cap) : 0u;
 }
 
 // ----------------------------------------------------------- batched form

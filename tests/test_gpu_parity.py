@@ -155,10 +155,19 @@ def test_policies_agree(pvt, make):
     dag = gpu_dag(pvt, rp, col)
     out = {}
     nosplit, mixed = (0,) * 7, (0, 0, 1, 0, 1, 0, 1)
-    for persistent, chunk, split in [(True, 4, None), (False, 1, None), (True, 1, nosplit), (True, 32, mixed)]:
-        dag.set_policy(persistent=persistent, chunk=chunk, split=split)
-        out[(persistent, chunk, split)] = pvt.to_ints(dag.count_global(kmax=ref["kmax"]))
+    walked = {}
+    for persistent, chunk, split, frames in [(True, 4, None, True), (False, 1, None, False), (True, 1, nosplit, True),
+                                             (True, 32, mixed, True), (True, 4, None, False), (True, 1, nosplit, False)]:
+        dag.set_policy(persistent=persistent, chunk=chunk, split=split, frames=frames)
+        out[(persistent, chunk, split, frames)] = pvt.to_ints(dag.count_global(kmax=ref["kmax"]))
+        st = dag.stats()
+        # the same tree whichever kernels walk it
+        walked[(persistent, chunk, split, frames)] = (st["sct_nodes"], st["sct_leaves"], st["pivot_words"])
+        assert sum(st["class_words"]) + st["frame_words"] == st["pivot_words"]
+        if not (persistent and frames):
+            assert st["frame_words"] == 0 and st["frames"] == 0
     assert all(v == ref["C"] for v in out.values())
+    assert len(set(walked.values())) == 1
     dag.free()
 
 
@@ -303,3 +312,37 @@ def test_errors(pvt):
     # the library stays usable afterwards
     assert pvt.to_ints(dag.count_global())[3] == math.comb(10, 3)
     torch.cuda.synchronize()
+
+
+# ------------------------------------------------ root ranges, checkpoints
+
+@pytest.mark.parametrize("make", [lambda: graphgen.workload("er2k_d20_clique30"),
+                                  lambda: graphs.clique_minus_random(300, 14, 7),
+                                  lambda: graphgen.generate(3000, er_avg_deg=12.0, planted=[(6, 20, 70, 0.9)], seed=13),
+                                  lambda: graphgen.workload("cl500k_m8m_b2.3_clq200")])
+def test_root_ranges_checkpoint(pvt, make):
+    """Histograms of disjoint root ranges add up to the whole count: walk
+    [0, n) in uneven pieces, passing the histogram through host memory
+    between pieces (a checkpoint), combine once; equals the oracle and the
+    one-call global count, word for word.  An empty range changes nothing."""
+    import torch
+    rp, col = make()
+    n = len(rp) - 1
+    ref = oracle.count(rp, col, threads=os.cpu_count() or 1)
+    K = ref["kmax"]
+    dag = gpu_dag(pvt, rp, col)
+    cuts = sorted({0, n, n // 7, n // 3, (2 * n) // 3, n - 1})
+    hist = None
+    for a, b in zip(cuts[:-1], cuts[1:]):
+        hist = dag.count_hist(a, b, hist=hist, kmax=K)
+        hist = hist.cpu().to("cuda:0")  # checkpoint round trip
+    before = hist.clone()
+    dag.count_hist(5, 5, hist=hist, kmax=K)
+    assert torch.equal(before, hist)
+    assert pvt.to_ints(dag.combine_hist(hist, kmax=K)) == ref["C"]
+    assert pvt.to_ints(dag.count_global(kmax=K)) == ref["C"]
+    # one call over [0, n) gives the same histogram
+    assert torch.equal(dag.count_hist(0, n, kmax=K), hist)
+    with pytest.raises(pvt.PivoterError):
+        dag.count_hist(3, 2, kmax=K)
+    dag.free()
