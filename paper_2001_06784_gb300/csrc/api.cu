@@ -1,5 +1,7 @@
 // C ABI entry points of libpivoter (declared in include/pivoter.h).
+#include <mutex>
 #include <new>
+#include <vector>
 #include <string>
 
 #include "pvt_internal.cuh"
@@ -57,42 +59,163 @@ void stats_reset(pvt_dag *g)
     for (int i = 0; i < NPHASE; ++i) g->phase_used[i] = false;
 }
 
+// Per-device resources that every dag needs whatever its graph -- status
+// and statistics words, pinned host copies, queue counters, side streams,
+// events, the Pascal table -- outlive their dag: pvt_dag_free hands them
+// back to a pool and the next pvt_orient on that device takes them, which
+// saves their creation (synchronous allocations, stream and event set-up)
+// on every call.
+struct DagRes {
+    int device = -1;
+    unsigned *d_err = nullptr, *d_q = nullptr, *h_err = nullptr;
+    unsigned long long *d_stats = nullptr, *h_stats = nullptr;
+    uint32_t *qctl = nullptr;
+    cudaEvent_t ev_t0[NPHASE] = {}, ev_t1[NPHASE] = {}, ev_fork = nullptr, ev_join[NCLASS] = {};
+    cudaStream_t side[NCLASS] = {};
+    DevBuf<unsigned long long> binom;
+    int binom_rows = 0, binom_W = 0;
+};
+
+static std::mutex g_res_mu;
+static std::vector<DagRes> g_res_pool;
+
+static cudaError_t res_create(int device, DagRes &r)
+{
+    r.device = device;
+    cudaError_t e = cudaMalloc(&r.d_err, sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMalloc(&r.d_q, 16 * sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMalloc(&r.d_stats, 16 * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMalloc(&r.qctl, NCLASS * 128 * sizeof(uint32_t));
+    for (int i = 0; i < NPHASE && e == cudaSuccess; ++i) {
+        e = cudaEventCreate(&r.ev_t0[i]);
+        if (e == cudaSuccess) e = cudaEventCreate(&r.ev_t1[i]);
+    }
+    if (e == cudaSuccess) e = cudaMallocHost(&r.h_err, sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMallocHost(&r.h_stats, 16 * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&r.ev_fork, cudaEventDisableTiming);
+    for (int c = 0; c < NCLASS && e == cudaSuccess; ++c) {
+        e = cudaStreamCreateWithFlags(&r.side[c], cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&r.ev_join[c], cudaEventDisableTiming);
+    }
+    return e;
+}
+
+static void res_destroy(DagRes &r)
+{
+    for (int c = 0; c < NCLASS; ++c) {
+        if (r.side[c]) { cudaStreamSynchronize(r.side[c]); cudaStreamDestroy(r.side[c]); }
+        if (r.ev_join[c]) cudaEventDestroy(r.ev_join[c]);
+    }
+    if (r.ev_fork) cudaEventDestroy(r.ev_fork);
+    for (int i = 0; i < NPHASE; ++i) {
+        if (r.ev_t0[i]) cudaEventDestroy(r.ev_t0[i]);
+        if (r.ev_t1[i]) cudaEventDestroy(r.ev_t1[i]);
+    }
+    cudaFree(r.d_err);
+    cudaFree(r.d_q);
+    cudaFree(r.d_stats);
+    cudaFree(r.qctl);
+    cudaFree(r.binom.p);
+    if (r.h_err) cudaFreeHost(r.h_err);
+    if (r.h_stats) cudaFreeHost(r.h_stats);
+    r = DagRes{};
+}
+
+// A resource set for `device` (current), from the pool or new.
+static cudaError_t res_take(int device, DagRes &r)
+{
+    {
+        std::lock_guard<std::mutex> lk(g_res_mu);
+        for (size_t i = 0; i < g_res_pool.size(); ++i)
+            if (g_res_pool[i].device == device) {
+                r = g_res_pool[i];
+                g_res_pool[i] = g_res_pool.back();
+                g_res_pool.pop_back();
+                return cudaSuccess;
+            }
+    }
+    cudaError_t e = res_create(device, r);
+    if (e != cudaSuccess) res_destroy(r);
+    return e;
+}
+
+static void res_to_dag(const DagRes &r, pvt_dag *g)
+{
+    g->d_err = r.d_err;
+    g->d_q = r.d_q;
+    g->d_stats = r.d_stats;
+    g->qctl = r.qctl;
+    g->h_err = r.h_err;
+    g->h_stats = r.h_stats;
+    for (int i = 0; i < NPHASE; ++i) {
+        g->ev_t0[i] = r.ev_t0[i];
+        g->ev_t1[i] = r.ev_t1[i];
+    }
+    g->ev_fork = r.ev_fork;
+    for (int c = 0; c < NCLASS; ++c) {
+        g->ev_join[c] = r.ev_join[c];
+        g->side[c] = r.side[c];
+    }
+    g->binom = r.binom;
+    g->binom_rows = r.binom_rows;
+    g->binom_W = r.binom_W;
+}
+
 static void dag_release(pvt_dag *g)
 {
     if (!g) return;
-    cudaStreamSynchronize(0);
     drop_graph(g);
+    // nothing of this dag is in flight once its side streams are idle: every
+    // entry point synchronises the caller's stream before it returns
+    for (int c = 0; c < NCLASS; ++c)
+        if (g->side[c]) cudaStreamSynchronize(g->side[c]);
+    cudaStream_t fs = g->side[0];
+    auto release = [&](void *p) {
+        if (p) cudaFreeAsync(p, fs);
+    };
+    release(g->rnd);
+    release(g->core);
+    release(g->orow);
+    release(g->ocol);
+    release(g->oeid);
+    release(g->roots);
+    release(g->hist.p);
     for (int c = 0; c < NCLASS; ++c) {
-        if (g->side[c]) { cudaStreamSynchronize(g->side[c]); cudaStreamDestroy(g->side[c]); }
-        if (g->ev_join[c]) cudaEventDestroy(g->ev_join[c]);
+        release(g->rootbuf[c].p);
+        release(g->qframes[c].p);
+        release(g->qready[c].p);
+        release(g->gstack[c].p);
     }
-    if (g->ev_fork) cudaEventDestroy(g->ev_fork);
+    release(g->cframes.p);
+    release(g->range_roots.p);
+    release(g->range_pos.p);
+    if (fs) cudaStreamSynchronize(fs);
+    DagRes r;
+    r.device = g->device;
+    r.d_err = g->d_err;
+    r.d_q = g->d_q;
+    r.d_stats = g->d_stats;
+    r.qctl = g->qctl;
+    r.h_err = g->h_err;
+    r.h_stats = g->h_stats;
     for (int i = 0; i < NPHASE; ++i) {
-        if (g->ev_t0[i]) cudaEventDestroy(g->ev_t0[i]);
-        if (g->ev_t1[i]) cudaEventDestroy(g->ev_t1[i]);
+        r.ev_t0[i] = g->ev_t0[i];
+        r.ev_t1[i] = g->ev_t1[i];
     }
-    cudaDeviceSynchronize();
-    cudaFree(g->rnd);
-    cudaFree(g->core);
-    cudaFree(g->orow);
-    cudaFree(g->ocol);
-    cudaFree(g->oeid);
-    cudaFree(g->roots);
-    cudaFree(g->d_err);
-    cudaFree(g->d_q);
-    cudaFree(g->hist.p);
-    cudaFree(g->binom.p);
+    r.ev_fork = g->ev_fork;
     for (int c = 0; c < NCLASS; ++c) {
-        cudaFree(g->rootbuf[c].p);
-        cudaFree(g->qframes[c].p);
-        cudaFree(g->qready[c].p);
+        r.ev_join[c] = g->ev_join[c];
+        r.side[c] = g->side[c];
     }
-    cudaFree(g->qctl);
-    cudaFree(g->cframes.p);
-    for (int c = 0; c < NCLASS; ++c) cudaFree(g->gstack[c].p);
-    cudaFree(g->d_stats);
-    if (g->h_err) cudaFreeHost(g->h_err);
-    if (g->h_stats) cudaFreeHost(g->h_stats);
+    r.binom = g->binom;
+    r.binom_rows = g->binom_rows;
+    r.binom_W = g->binom_W;
+    if (r.d_err && r.side[NCLASS - 1] && r.h_stats) {
+        std::lock_guard<std::mutex> lk(g_res_mu);
+        g_res_pool.push_back(r);
+    } else {
+        res_destroy(r);  // a set that was never complete
+    }
     delete g;
 }
 
@@ -121,20 +244,10 @@ pvt_status pvt_orient(int64_t n, int64_t nnz, const int64_t *row_ptr, const uint
     auto fail = [&](pvt_status x) { dag_release(g); return x; };
     cudaError_t e = cudaGetDevice(&g->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&g->num_sms, cudaDevAttrMultiProcessorCount, g->device);
-    if (e == cudaSuccess) e = cudaMalloc(&g->d_err, sizeof(unsigned));
-    if (e == cudaSuccess) e = cudaMalloc(&g->d_q, 16 * sizeof(unsigned));
-    if (e == cudaSuccess) e = cudaMalloc(&g->d_stats, 16 * sizeof(unsigned long long));
-    if (e == cudaSuccess) e = cudaMalloc(&g->qctl, NCLASS * 128 * sizeof(uint32_t));
-    for (int i = 0; i < NPHASE && e == cudaSuccess; ++i) {
-        e = cudaEventCreate(&g->ev_t0[i]);
-        if (e == cudaSuccess) e = cudaEventCreate(&g->ev_t1[i]);
-    }
-    if (e == cudaSuccess) e = cudaMallocHost(&g->h_err, sizeof(unsigned));
-    if (e == cudaSuccess) e = cudaMallocHost(&g->h_stats, 16 * sizeof(unsigned long long));
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&g->ev_fork, cudaEventDisableTiming);
-    for (int c = 0; c < NCLASS && e == cudaSuccess; ++c) {
-        e = cudaStreamCreateWithFlags(&g->side[c], cudaStreamNonBlocking);
-        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&g->ev_join[c], cudaEventDisableTiming);
+    if (e == cudaSuccess) {
+        DagRes r;
+        e = res_take(g->device, r);
+        if (e == cudaSuccess) res_to_dag(r, g);
     }
     if (e == cudaSuccess) {
         // keep stream-ordered scratch cached across calls instead of handing it

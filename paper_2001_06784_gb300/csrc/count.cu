@@ -145,8 +145,10 @@ __global__ void __launch_bounds__(256) k_combine(const unsigned long long *__res
 
 static pvt_status ensure_binom(pvt_dag *g, int W, cudaStream_t s)
 {
+    // a table with more rows holds this one as its prefix (entry (a, b) sits
+    // at (a(a+1)/2 + b) W whatever the row count), so a pooled table is reused
     const int rows = g->alpha + 3;
-    if (g->binom_rows == rows && g->binom_W == W) return PVT_OK;
+    if (g->binom_rows >= rows && g->binom_W == W) return PVT_OK;
     pvt_status st = grow(g->binom, (size_t)rows * (rows + 1) / 2 * W, s);
     if (st != PVT_OK) return st;
     k_binom<<<1, 1024, 0, s>>>(g->binom.p, rows, W, g->d_err);

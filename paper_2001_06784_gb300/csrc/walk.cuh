@@ -665,22 +665,37 @@ __device__ void walk_root(WarpWork<NW> &Wk, unsigned long long *shist, const Cou
     if (lane == 0) Wk.off[0] = 0;
     for (int t = lane; t < d * RS; t += 32) Wk.adj[t] = 0;
     __syncwarp();
+    // entry t of the concatenated out-lists belongs to member lo, the largest
+    // i with off[i] <= t; a lane's entries rise, so lo only moves forward.
+    // Four entries per lane per round keep four loads of ocol in flight.
     const uint32_t T = base;
-    for (uint32_t t = lane; t < T; t += 32) {
-        int lo = 0, hi = d - 1;  // largest i with off[i] <= t
-        while (lo < hi) {
-            int mid = (lo + hi + 1) >> 1;
-            if (Wk.off[mid] <= t) lo = mid; else hi = mid - 1;
+    int lo = 0;
+    for (uint32_t t0 = lane; t0 < T; t0 += 128) {
+        uint32_t x[4];
+        int mi[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const uint32_t t = t0 + 32u * q;
+            mi[q] = -1;
+            if (t < T) {
+                while (Wk.off[lo + 1] <= t) ++lo;  // stops by off[d] = T > t
+                mi[q] = lo;
+                x[q] = A.ocol[Wk.rs[lo] + (t - Wk.off[lo])];
+            }
         }
-        uint32_t x = A.ocol[Wk.rs[lo] + (t - Wk.off[lo])];
-        int a = 0, b = d;
-        while (a < b) {
-            int mid = (a + b) >> 1;
-            if (Wk.ids[mid] < x) a = mid + 1; else b = mid;
-        }
-        if (a < d && Wk.ids[a] == x) {
-            atomicOr(&Wk.adj[lo * RS + (a >> 5)], 1u << (a & 31));
-            atomicOr(&Wk.adj[a * RS + (lo >> 5)], 1u << (lo & 31));
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            if (mi[q] < 0) continue;
+            int a = 0, b = d;
+            while (a < b) {
+                int mid = (a + b) >> 1;
+                if (Wk.ids[mid] < x[q]) a = mid + 1; else b = mid;
+            }
+            if (a < d && Wk.ids[a] == x[q]) {
+                const int u = mi[q];
+                atomicOr(&Wk.adj[u * RS + (a >> 5)], 1u << (a & 31));
+                atomicOr(&Wk.adj[a * RS + (u >> 5)], 1u << (u & 31));
+            }
         }
     }
     __syncwarp();
