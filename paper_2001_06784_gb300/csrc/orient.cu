@@ -64,6 +64,7 @@ struct PeelState {
     unsigned done;        // queue entries fully processed so far
     unsigned pad2[31];
     unsigned min_next[2]; // lower bound of the next level's smallest residual degree (by level parity)
+    unsigned scan_end[2]; // end of the queue positions the scan pushed (by level parity)
     unsigned alive_cnt[2];// length of the alive list being built (by level parity)
     unsigned bar_count;   // grid barrier arrivals
     unsigned bar_gen;     // grid barrier generation
@@ -89,6 +90,9 @@ constexpr int TAIL_THREADS = 1024;
 constexpr unsigned long long BARRIER_LIMIT_NS = 4000000000ull;  // 4 s
 constexpr unsigned long long CASCADE_LIMIT_NS = 4000000000ull;  // 4 s without progress
 constexpr uint32_t EMPTY = 0xFFFFFFFFu;
+// bulk processing of a level's scan pushes: from this many pushes on, one
+// thread per pushed vertex, for out-lists up to BULK_LANE_MAX entries
+constexpr unsigned BULK_MIN = 4096, BULK_LANE_MAX = 64;
 
 // Grid-wide barrier for a cooperative launch, with a bounded wait: on
 // timeout it sets DERR_TIMEOUT and every block leaves the kernel.
@@ -152,7 +156,7 @@ __device__ bool grid_barrier(PeelState *st, unsigned *err)
 // Out-degree bound: a neighbour pushed after v never lowered deg[v] (v was
 // already removed when it was processed), so at v's push deg[v] <= k counts
 // all of v's later neighbours.
-__global__ void __launch_bounds__(1024) k_peel(int64_t n, const int64_t *__restrict__ rp,
+__global__ void __launch_bounds__(1024, 1) k_peel(int64_t n, const int64_t *__restrict__ rp,
                                                const uint32_t *__restrict__ col, uint32_t *deg,
                                                uint32_t *rnd, uint32_t *core, uint32_t *lq, uint32_t *alive,
                                                PeelState *st, unsigned tail_max, unsigned *err)
@@ -217,7 +221,10 @@ __global__ void __launch_bounds__(1024) k_peel(int64_t n, const int64_t *__restr
             const unsigned below = (1u << lane) - 1u;
             if (bt) {
                 unsigned at = 0;
-                if (lane == 0) at = atomicAdd(&st->tail, (unsigned)__popc(bt));
+                if (lane == 0) {
+                    at = atomicAdd(&st->tail, (unsigned)__popc(bt));
+                    atomicMax(&st->scan_end[q], at + (unsigned)__popc(bt));
+                }
                 at = __shfl_sync(FULL, at, 0);
                 if (take) {
                     const unsigned pos = at + __popc(bt & below);
@@ -237,10 +244,66 @@ __global__ void __launch_bounds__(1024) k_peel(int64_t n, const int64_t *__restr
             }
         }
         if (!grid_barrier(st, err)) return;
+        // every scan push happened before the barrier and nothing moves
+        // scan_end during the cascade, so every thread reads the same end
+        const unsigned se = max(vst->scan_end[q], t_start);
         if (tid == 0) {
             st->levels++;
             st->min_next[q] = NOT_REMOVED;  // read by every thread above; next written at level + 1
             st->alive_cnt[q] = 0;
+            st->scan_end[q ^ 1u] = 0;       // last read at level - 1; next written at level + 1
+        }
+        // ---- bulk: when the scan pushed many vertices, one thread per pushed
+        // vertex lowers its neighbours' degrees (lists longer than
+        // BULK_LANE_MAX by the whole warp); the claims below then start at se
+        const bool bulk = se - t_start >= BULK_MIN;
+        if (bulk) {
+            unsigned ndone = 0;
+            for (int64_t base = (int64_t)t_start + tid - lane; base < (int64_t)se; base += nthreads) {
+                const int64_t i = base + lane;
+                uint32_t v = 0;
+                int64_t b = 0, e = 0;
+                if (i < (int64_t)se) {
+                    v = lq[i];
+                    b = rp[v];
+                    e = rp[v + 1];
+                    ++ndone;
+                }
+                const bool mine = e - b <= (int64_t)BULK_LANE_MAX;
+                if (mine) {
+                    for (int64_t j = b; j < e; ++j) {
+                        const uint32_t u = col[j];
+                        const unsigned old = atomicSub(&deg[u], 1u);
+                        if (old == k + 1) {
+                            const unsigned pos = atomicAdd(&st->tail, 1u);
+                            rnd[u] = pos;
+                            core[u] = k;
+                            *(volatile uint32_t *)(lq + pos) = u;
+                        } else if (old > k + 1) {
+                            mnext = min(mnext, old - 1);
+                        }
+                    }
+                }
+                for (unsigned big = __ballot_sync(FULL, !mine); big; big &= big - 1) {
+                    const int src = __ffs(big) - 1;
+                    const int64_t bb = __shfl_sync(FULL, b, src), ee = __shfl_sync(FULL, e, src);
+                    for (int64_t j = bb + lane; j < ee; j += 32) {
+                        const uint32_t u = col[j];
+                        const unsigned old = atomicSub(&deg[u], 1u);
+                        if (old == k + 1) {
+                            const unsigned pos = atomicAdd(&st->tail, 1u);
+                            rnd[u] = pos;
+                            core[u] = k;
+                            *(volatile uint32_t *)(lq + pos) = u;
+                        } else if (old > k + 1) {
+                            mnext = min(mnext, old - 1);
+                        }
+                    }
+                }
+            }
+            __threadfence();  // these entries' pushes are counted before they are done
+            ndone = __reduce_add_sync(FULL, ndone);
+            if (lane == 0 && ndone) atomicAdd(&st->done, ndone);
         }
         // ---- cascade, on as many warps per block as the waiting entries need
         // (at least two per block; warps that read the counters late may see
@@ -254,7 +317,7 @@ __global__ void __launch_bounds__(1024) k_peel(int64_t n, const int64_t *__restr
                 int got = 0;  // 1: vertex in `v`, 2: level done, 3: error
                 uint32_t v = 0;
                 if (lane == 0) {
-                    if (claim == EMPTY) claim = atomicAdd(&st->head, 1u);
+                    if (claim == EMPTY) claim = atomicAdd(&st->head, 1u) + (bulk ? se - t_start : 0u);
                     unsigned spins = 0, last = 0xFFFFFFFFu;
                     unsigned long long t0 = 0;
                     for (;;) {
