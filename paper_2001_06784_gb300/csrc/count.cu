@@ -168,7 +168,7 @@ static pvt_status launch_frames(pvt_dag *g, const CountArgs &base, cudaStream_t 
     if ((st = grow(g->qframes[0], (size_t)SPLIT_QCAP * FRAME_WORDS, s)) != PVT_OK) return st;
     if ((st = grow(g->qready[0], (size_t)SPLIT_QCAP * 2, s)) != PVT_OK) return st;
     PVT_CK(cudaMemsetAsync(g->qready[0].p, 0, (size_t)SPLIT_QCAP * 2 * sizeof(uint32_t), s));
-    k_frames_init<<<1, 128, 0, s>>>(g->qctl, A.emit_count, A.emit_cap, A.frame_cursor);
+    k_frames_init<<<1, 128, 0, s>>>(g->qctl, A.emit_count, A.emit_cap);
     PVT_CK(cudaGetLastError());
     A.qframes = g->qframes[0].p;
     A.qready = g->qready[0].p;
@@ -204,13 +204,10 @@ static pvt_status launch_all(pvt_dag *g, const CountArgs &A0, cudaStream_t s)
     const bool frames = MODE == MODE_GLOBAL && g->policy.frames && g->policy.persistent && heavy > 0;
     if (frames) {
         const unsigned cap = (unsigned)std::min<int64_t>(std::max<int64_t>(64 * heavy, 1 << 16), 1 << 22);
-        pvt_status st = grow(g->cframes, (size_t)cap * (FRAME_WORDS + 1), s);
+        pvt_status st = grow(g->cframes, (size_t)cap * FRAME_WORDS, s);
         if (st != PVT_OK) return st;
         A.emit = g->cframes.p;
-        A.emit_ready = g->cframes.p + (size_t)cap * FRAME_WORDS;
-        PVT_CK(cudaMemsetAsync(A.emit_ready, 0, (size_t)cap * sizeof(uint32_t), s));
         A.emit_count = g->d_q + 8;
-        A.frame_cursor = g->d_q + 9;
         A.emit_cap = cap;
     }
     // heavy classes on side streams so that they overlap the light ones (or

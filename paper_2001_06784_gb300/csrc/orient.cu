@@ -460,7 +460,7 @@ __global__ void k_tail_fill(const int64_t *__restrict__ rp, const uint32_t *__re
 // degrees, the removal queue and the row offsets live in shared memory,
 // the residual adjacency (local ids) in global memory.  Removal times
 // continue the grid peel's numbering.
-__global__ void __launch_bounds__(TAIL_THREADS) k_peel_tail(const int64_t *__restrict__ roff,
+__global__ void __launch_bounds__(TAIL_THREADS, 1) k_peel_tail(const int64_t *__restrict__ roff,
                                                             const uint32_t *__restrict__ rcol,
                                                             const uint32_t *__restrict__ rdeg,
                                                             const uint32_t *__restrict__ tv, uint32_t *rnd,
@@ -495,6 +495,9 @@ __global__ void __launch_bounds__(TAIL_THREADS) k_peel_tail(const int64_t *__res
     unsigned top = st->top_level, levels = 0;
     auto push = [&](unsigned i, unsigned k) {
         atomicOr(&sgone[i >> 5], 1u << (i & 31));
+        // the warp that takes this entry runs on this SM: bring the start of
+        // the vertex's residual row into L1 for it
+        asm volatile("prefetch.global.L1 [%0];" ::"l"(rcol + soff[i]));
         const unsigned pos = atomicAdd(&s_tail, 1u);
         rnd[tv[i]] = base + pos;
         core[tv[i]] = k;

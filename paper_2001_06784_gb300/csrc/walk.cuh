@@ -146,8 +146,6 @@ struct CountArgs {
     uint32_t *emit;             // [emit_cap][FRAME_WORDS]
     unsigned *emit_count;       // frames reserved so far (may pass emit_cap)
     unsigned emit_cap;
-    uint32_t *emit_ready;       // [emit_cap]: 1 once frame i is written
-    unsigned *frame_cursor;     // frames taken by idle warps of the class kernels
 };
 
 // Work queue of a split launch, a ring of qcap slots.  Idle warps take a
@@ -602,9 +600,6 @@ __device__ void walk_compact(WarpWork<NW> &Wk, unsigned long long *shist, const 
                 fr[2] = S1;
                 fr[3] = (uint32_t)A.cls;
             }
-            __threadfence();
-            __syncwarp();
-            if (lane == 0) atomicExch(A.emit_ready + i, 1u);
             return;
         }
     }
@@ -936,56 +931,24 @@ __device__ __forceinline__ void bind_warp(WarpWork<NW> &Wk, unsigned char *local
 }
 
 // Lane 0 of a split launch: the next item -- 2 with v = a fresh item index
-// below nitems, 1 with v = the ticket of a donated frame, 4 with v = an
-// emitted frame taken while waiting (steal: the class kernels' idle warps
-// walk frames of the two-phase count instead of sleeping, as long as their
-// own launch still has work outstanding), 3 when no work is left (or an
-// error or a timeout ended the launch).  A ticket taken and not yet served
-// stays in `pending` across calls.
-__device__ __forceinline__ int queue_take(const CountArgs &A, unsigned nitems, unsigned &v, bool steal,
-                                          unsigned &pending)
+// below nitems, 1 with v = the ticket of a donated frame, 3 when no work is
+// left (or an error or a timeout ended the launch).
+__device__ __forceinline__ int queue_take(const CountArgs &A, unsigned nitems, unsigned &v)
 {
-    constexpr unsigned NONE = 0xFFFFFFFFu;
-    if (pending == NONE) {
-        if (vload(A.qctl + Q_ROOT) < nitems) {
-            const unsigned rr = atomicAdd(A.qctl + Q_ROOT, 1u);
-            if (rr < nitems) { v = rr; return 2; }
-        }
-        pending = atomicAdd(A.qctl + Q_HEAD, 1u);  // a ticket for the next donated frame
+    if (vload(A.qctl + Q_ROOT) < nitems) {
+        const unsigned rr = atomicAdd(A.qctl + Q_ROOT, 1u);
+        if (rr < nitems) { v = rr; return 2; }
     }
-    const unsigned t = pending;
+    // a ticket for the next donated frame; wait on its own slot
     int kind = 0;
+    const unsigned t = atomicAdd(A.qctl + Q_HEAD, 1u);
     unsigned last_out = 0xFFFFFFFFu, nap = 64;
     unsigned long long t0 = global_ns();
     const unsigned slot = t & (A.qcap - 1u);
     for (;;) {
-        if (vload(A.qready + slot) == t + 1u) { kind = 1; v = t; pending = NONE; break; }
+        if (vload(A.qready + slot) == t + 1u) { kind = 1; v = t; break; }
         const unsigned out = vload(A.qctl + Q_OUT);
         if (out == 0 || (vload(A.err) & (DERR_STACK | DERR_RANGE | DERR_TIMEOUT))) { kind = 3; break; }
-        if (steal && vload(A.frame_cursor) < min(vload(A.emit_count), A.emit_cap)) {
-            // join this launch's outstanding items first (only from a non-zero
-            // count: once it reaches zero it never rises again, so no waiting
-            // warp has left), so that subtrees the frame's walk donates are
-            // still served; then claim the frame
-            unsigned o = out;
-            bool joined = false;
-            while (o != 0) {
-                const unsigned w = atomicCAS(A.qctl + Q_OUT, o, o + 1u);
-                if (w == o) { joined = true; break; }
-                o = w;
-            }
-            if (joined) {
-                unsigned c = vload(A.frame_cursor);
-                const unsigned e = min(vload(A.emit_count), A.emit_cap);
-                while (c < e) {
-                    const unsigned w = atomicCAS(A.frame_cursor, c, c + 1u);
-                    if (w == c) break;
-                    c = w;
-                }
-                if (c < e) { v = c; return 4; }  // the caller gives the item back when done
-                atomicSub(A.qctl + Q_OUT, 1u);
-            }
-        }
         if (out != last_out) { last_out = out; t0 = global_ns(); }
         else if (global_ns() - t0 > SPLIT_IDLE_LIMIT_NS) { atomicOr(A.err, DERR_TIMEOUT); kind = 3; break; }
         __nanosleep(nap);
@@ -993,21 +956,6 @@ __device__ __forceinline__ int queue_take(const CountArgs &A, unsigned nitems, u
     }
     if (kind == 1) __threadfence();
     return kind;
-}
-
-// Lane 0: wait until emitted frame v is written (bounded); false on timeout.
-__device__ __forceinline__ bool emitted_ready(const CountArgs &A, unsigned v)
-{
-    const unsigned long long t0 = global_ns();
-    while (vload(A.emit_ready + v) == 0u) {
-        if (global_ns() - t0 > SPLIT_SLOT_LIMIT_NS) {
-            atomicOr(A.err, DERR_TIMEOUT);
-            return false;
-        }
-        __nanosleep(32);
-    }
-    __threadfence();
-    return true;
 }
 
 // Copy donated frame t out of the ring into fb and release its slot.
@@ -1045,29 +993,11 @@ __global__ void __launch_bounds__(32 * warps_per_block<NW>())
     unsigned qi = 0, qend = 0;
     if (SPLIT) {
         // heavy roots and donated subtree frames from one device work queue
-        unsigned pending = 0xFFFFFFFFu;  // lane 0: ticket waiting to be served
         for (;;) {
             unsigned v = 0;
-            int kind = lane == 0 ? queue_take(A, A.nroots, v, A.emit != nullptr, pending) : 0;
-            if (lane == 0 && kind == 4 && !emitted_ready(A, v)) {
-                atomicSub(A.qctl + Q_OUT, 1u);
-                kind = 3;
-            }
+            int kind = lane == 0 ? queue_take(A, A.nroots, v) : 0;
             kind = __shfl_sync(FULL, kind, 0);
             v = __shfl_sync(FULL, v, 0);
-            if (kind == 4) {
-                // an emitted frame, walked here instead of waiting idle (it
-                // counts as an item of this launch until it is done)
-                const uint32_t *fr = A.emit + (size_t)v * FRAME_WORDS;
-                const uint32_t r1 = __ldcg(fr + 4 + lane), S1 = __ldcg(fr + 2), hp0 = __ldcg(fr + 1);
-                Clock clk;
-                compact_loop<NW, SHIST, true>(ww[wid], shist, A, lane, r1, S1, (int)(hp0 >> 16),
-                                              (int)(hp0 & 0xFFFFu), wc, nullptr, clk);
-                wc.fold();
-                __syncwarp();
-                if (lane == 0) atomicSub(A.qctl + Q_OUT, 1u);
-                continue;
-            }
             if (kind == 3) break;
             if (kind == 1) {
                 // copy the frame out and release its ring slot at once
@@ -1239,7 +1169,6 @@ __global__ void __launch_bounds__(32 * FRAME_WPB) k_walk_frames(CountArgs A)
         __syncthreads();
     }
     unsigned cur = 0, end = 0;  // lane 0: claimed emitted frames [cur, end)
-    unsigned pending = 0xFFFFFFFFu;
     for (;;) {
         unsigned v = 0;
         int kind = 0;
@@ -1261,7 +1190,7 @@ __global__ void __launch_bounds__(32 * FRAME_WPB) k_walk_frames(CountArgs A)
                     for (; a < b; a += 128) asm volatile("prefetch.global.L2 [%0];" ::"l"(a));
                 }
             }
-            if (kind == 0) kind = queue_take(A, 0u, v, false, pending);
+            if (kind == 0) kind = queue_take(A, 0u, v);
         }
         kind = __shfl_sync(FULL, kind, 0);
         v = __shfl_sync(FULL, v, 0);
@@ -1294,13 +1223,10 @@ __global__ void __launch_bounds__(32 * FRAME_WPB) k_walk_frames(CountArgs A)
 
 // Queue counters of the frame walk: outstanding items = the emitted frames
 // (read on the device: the count is final once the wide walks are done).
-static __global__ void k_frames_init(uint32_t *qctl, const unsigned *emit_count, unsigned cap,
-                                     const unsigned *frame_cursor)
+static __global__ void k_frames_init(uint32_t *qctl, const unsigned *emit_count, unsigned cap)
 {
-    // the frames below frame_cursor were walked by idle warps of the class kernels
-    const unsigned nframes = min(*emit_count, cap), taken = min(*frame_cursor, nframes);
     for (int i = threadIdx.x; i < QCTL_WORDS; i += blockDim.x)
-        qctl[i] = i == Q_OUT ? nframes - taken : (i == Q_ROOT ? taken : 0u);
+        qctl[i] = i == Q_OUT ? min(*emit_count, cap) : 0u;
 }
 
 // ----------------------------------------------------------- batched form
