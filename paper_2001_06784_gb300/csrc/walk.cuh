@@ -66,8 +66,7 @@ struct WarpWork {
         memH = path + (D + 2);
         memP = memH + (D + 2);
     }
-    uint32_t stk1[33];           // one-word walk of a compacted subtree: S
-    uint32_t hp1[33];            //   and (h << 16) | p
+    uint2 cstk[33];              // one-word walk of a compacted subtree: (S, (h << 16) | p)
     uint16_t cmap[32];           // compacted index -> member index
     uint32_t fbuf[36];           // copy of a donated frame taken from the queue
     __device__ __forceinline__ uint32_t *stk() { return GSTACK ? gstk : stk_s; }
@@ -431,23 +430,31 @@ __device__ void compact_loop(WarpWork<NW> &Wk, unsigned long long *shist, const 
                              Clock &clk)
 {
     auto tally = [&](int hh, int pp) { tally_leaf<SHIST>(shist, A, lane, hh, pp); };
+    // this call's nodes, leaves and pivot words (every lane alike; at most a
+    // 32-member label's tree, so 32 bits hold them), added to wc on exit
+    unsigned cn = 0, cl = 0, cw = 0;
+    auto fold = [&]() {
+        wc.nodes += cn;
+        wc.leaves += cl;
+        wc.words += cw;
+    };
     int top = 0, bot = 0;
     for (;;) {
         const int s1 = __popc(S1);
-        wc.nodes++;
+        ++cn;
         clk.nodes++;
         bool closed = true;
         if (s1 == 0) {
-            wc.leaves++;
+            ++cl;
             tally(h, p);
         } else {
             const bool in = (S1 >> lane) & 1u;
             const uint32_t c = in ? __popc(r1 & S1) : 0u;
             const uint32_t best = __reduce_max_sync(FULL, in ? (((c + 1u) << 5) | (31u - lane)) : 0u);
             const uint32_t dsum = __reduce_add_sync(FULL, c);
-            wc.words += (unsigned long long)s1;
+            cw += (unsigned)s1;
             if (dsum == (uint32_t)s1 * (uint32_t)(s1 - 1)) {
-                wc.leaves++;
+                ++cl;
                 tally(h, p + s1);
             } else {
                 const int piv = 31 - (int)(best & 31u);
@@ -468,26 +475,26 @@ __device__ void compact_loop(WarpWork<NW> &Wk, unsigned long long *shist, const 
                 }
                 const int nR = __popc(R);
                 if (nR > 0) {
-                    if (SPLIT && bot > 0 && top + nR > 33) {
-                        __syncwarp();
-                        for (int t = lane; t < top - bot; t += 32) {
-                            Wk.stk1[t] = Wk.stk1[bot + t];
-                            Wk.hp1[t] = Wk.hp1[bot + t];
-                        }
-                        top -= bot;
-                        bot = 0;
-                        __syncwarp();
-                    }
                     if (top + nR > 33) {
-                        if (lane == 0) atomicOr(A.err, DERR_STACK);
-                        return;
+                        if (SPLIT && bot > 0) {
+                            // donated frames left room at the base: move the live ones down
+                            __syncwarp();
+                            for (int t = lane; t < top - bot; t += 32) Wk.cstk[t] = Wk.cstk[bot + t];
+                            top -= bot;
+                            bot = 0;
+                            __syncwarp();
+                        }
+                        if (top + nR > 33) {
+                            if (lane == 0) atomicOr(A.err, DERR_STACK);
+                            fold();
+                            return;
+                        }
                     }
                     __syncwarp();
                     if ((R >> lane) & 1u) {
                         const uint32_t low = (1u << lane) - 1u;
                         const int f = top + __popc(R & low);
-                        Wk.stk1[f] = r1 & S1 & ~(R0 & low);
-                        Wk.hp1[f] = ((uint32_t)(h + 1) << 16) | (uint32_t)p;
+                        Wk.cstk[f] = make_uint2(r1 & S1 & ~(R0 & low), ((uint32_t)(h + 1) << 16) | (uint32_t)p);
                     }
                     top += nR;
                     __syncwarp();
@@ -503,7 +510,7 @@ __device__ void compact_loop(WarpWork<NW> &Wk, unsigned long long *shist, const 
                                 for (int w = 0; w < NW; ++w) sz += __popc(Wk.stk()[*outer->bot * NW + w]);
                                 wide = sz >= DONATE_MIN_WIDE;
                             }
-                            if (!wide && top - bot >= 2 && __popc(Wk.stk1[bot]) >= DONATE_MIN_COMPACT) ndon = 1;
+                            if (!wide && top - bot >= 2 && __popc(Wk.cstk[bot].x) >= DONATE_MIN_COMPACT) ndon = 1;
                         }
                         wide = __shfl_sync(FULL, wide, 0);
                         ndon = __shfl_sync(FULL, ndon, 0);
@@ -517,8 +524,8 @@ __device__ void compact_loop(WarpWork<NW> &Wk, unsigned long long *shist, const 
                                 fr[4 + lane] = r1;
                                 if (lane == 0) {
                                     fr[0] = FRAME_COMPACT;
-                                    fr[1] = Wk.hp1[bot];
-                                    fr[2] = Wk.stk1[bot];
+                                    fr[1] = Wk.cstk[bot].y;
+                                    fr[2] = Wk.cstk[bot].x;
                                     fr[3] = (uint32_t)A.cls;
                                 }
                                 frame_publish(A, lane, t);
@@ -543,11 +550,13 @@ __device__ void compact_loop(WarpWork<NW> &Wk, unsigned long long *shist, const 
         if (!closed) continue;
         if (top == bot) break;
         --top;
-        S1 = Wk.stk1[top];
-        const uint32_t hp = Wk.hp1[top];
+        const uint2 e = Wk.cstk[top];
+        S1 = e.x;
+        const uint32_t hp = e.y;
         h = (int)(hp >> 16);
         p = (int)(hp & 0xFFFFu);
     }
+    fold();
     __syncwarp();
 }
 
