@@ -400,6 +400,7 @@ struct Clock {
     unsigned nodes = 0, next = 0;
     unsigned every = 16;  // nodes between looks at the queue
 };
+constexpr unsigned EMIT_CLOCK = 4;  // clock ticks per emitted frame
 
 // Hand wide frame f (of root qi, out-degree d) to the frame queue.
 template <int NW>
@@ -609,6 +610,10 @@ __device__ void walk_compact(WarpWork<NW> &Wk, unsigned long long *shist, const 
                 fr[2] = S1;
                 fr[3] = (uint32_t)A.cls;
             }
+            // an emission is where the wide walk spends its time: let it
+            // advance the donation clock, so that a heavy root's pending wide
+            // frames move to idle warps
+            clk.nodes += EMIT_CLOCK;
             return;
         }
     }
