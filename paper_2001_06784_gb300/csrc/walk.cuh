@@ -1218,7 +1218,7 @@ __global__ void __launch_bounds__(32 * FRAME_WPB) k_walk_frames(CountArgs A)
         }
         const uint32_t r1 = fr[4 + lane], S1 = fr[2], hp0 = fr[1];
         Clock clk;
-        clk.every = 64;
+        clk.every = 32;
         compact_loop<1, SHIST, true>(ww[wid], shist, A, lane, r1, S1, (int)(hp0 >> 16), (int)(hp0 & 0xFFFFu), wc,
                                      nullptr, clk);
         wc.fold();
