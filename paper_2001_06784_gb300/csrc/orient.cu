@@ -511,12 +511,19 @@ __global__ void __launch_bounds__(TAIL_THREADS, 1) k_peel_tail(const int64_t *__
         const unsigned k = s_min[q];
         ++levels;
         unsigned mnext = NOT_REMOVED;
-        // ---- scan
-        for (unsigned i = threadIdx.x; i < R; i += blockDim.x) {
-            if ((sgone[i >> 5] >> (i & 31)) & 1u) continue;
-            const unsigned d = sdeg[i];
-            if (d <= k) push(i, k);
-            else mnext = min(mnext, d);
+        // ---- scan of the vertices still present, 16 per thread from the
+        // removed bitmap (only the owner of a chunk pushes from it, so the
+        // bits it read do not change under it)
+        for (unsigned c = threadIdx.x; c < (R + 15) / 16; c += blockDim.x) {
+            const unsigned base = c * 16;
+            uint32_t live = (~sgone[c >> 1] >> (16 * (c & 1))) & 0xFFFFu;
+            if (base + 16 > R) live &= (1u << (R - base)) - 1u;
+            for (; live; live &= live - 1) {
+                const unsigned i = base + __ffs(live) - 1;
+                const unsigned d = sdeg[i];
+                if (d <= k) push(i, k);
+                else mnext = min(mnext, d);
+            }
         }
         __syncthreads();
         if (threadIdx.x == 0) s_min[q] = NOT_REMOVED;  // read above by every thread
