@@ -43,7 +43,7 @@ typedef enum pvt_status {
     PVT_EOVERFLOW = 4,   /* W words cannot hold every count of this graph */
     PVT_ECUDA = 5,       /* a CUDA call failed */
     PVT_ETIMEOUT = 6,    /* a bounded device-side wait expired */
-    PVT_EINTERNAL = 7    /* a device-side capacity check failed (a library bug) */
+    PVT_EINTERNAL = 7    /* a device-side capacity or consistency check failed (a library bug) */
 } pvt_status;
 
 /* Opaque, library-owned device state of one oriented graph. */
@@ -102,7 +102,11 @@ pvt_status pvt_dag_cores(const pvt_dag *dag, uint32_t *core, void *stream);
  *   kmax   >= 0; any value is accepted (entries above the clique number are 0)
  *   W      words per count, >= min_words (else PVT_EOVERFLOW before any launch)
  *   C      device uint64[kmax+1][W], written in full
- * Errors: PVT_EINVAL, PVT_EOVERFLOW, PVT_ENOMEM, PVT_ECUDA, PVT_EINTERNAL.
+ * Every root has exactly one all-pivot path (a leaf with h = 1), and the
+ * 2-cliques read off the leaves are the edges; for kmax >= 1 the device
+ * checks the first, for kmax >= 2 the second, before C is formed.
+ * Errors: PVT_EINVAL, PVT_EOVERFLOW, PVT_ENOMEM, PVT_ECUDA, PVT_EINTERNAL
+ * (a capacity check, or the path check above, failed).
  */
 pvt_status pvt_count_global(pvt_dag *dag, int32_t kmax, int32_t W, uint64_t *C, void *stream);
 
@@ -148,6 +152,8 @@ pvt_status pvt_count_local_edge(pvt_dag *dag, int32_t kmax, int32_t W, uint64_t 
  * Copying hist to the host after any range and back before the next is a
  * checkpoint; the histogram of disjoint ranges counted on different GPUs
  * (each with its own dag of the same graph) is their sum.
+ * For kmax >= 1 the device checks that row h = 1 gained exactly one leaf
+ * per root of the range (PVT_EINTERNAL otherwise).
  * Errors: PVT_EINVAL (NULL dag or hist, kmax < 0, begin < 0, end < begin),
  * others as pvt_count_global.
  */
@@ -293,7 +299,8 @@ pvt_status pvt_dag_autotune(pvt_dag *dag, int32_t kmax, int32_t W, uint64_t *C, 
  * call on a device shares the one array and clears what must start at zero;
  * calls whose work overlaps on the GPU (other streams, other host threads)
  * race on it and must be serialised by the caller.  The call returns once C
- * is complete and checked.
+ * is complete and checked (the root-path checks of pvt_count_global, every
+ * vertex being a root; PVT_EINTERNAL if they fail).
  */
 pvt_status pvt_count_global_noalloc(int64_t n, const int64_t *orow, const uint32_t *ocol, int32_t alpha,
                                     int32_t kmax, int32_t W, uint64_t *C, void *stream);

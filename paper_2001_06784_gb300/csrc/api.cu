@@ -37,6 +37,7 @@ pvt_status check_device(pvt_dag *g, cudaStream_t s, const char *what)
     if (e & DERR_TIMEOUT) { set_error(w + ": device-side wait timed out"); return PVT_ETIMEOUT; }
     if (e & DERR_OVERFLOW) { set_error(w + ": multi-word overflow"); return PVT_EOVERFLOW; }
     if (e & DERR_STACK) { set_error(w + ": DFS stack capacity exceeded"); return PVT_EINTERNAL; }
+    if (e & DERR_CHECK) { set_error(w + ": internal consistency check of the root paths failed"); return PVT_EINTERNAL; }
     set_error(w + ": device index check failed");
     return PVT_EINTERNAL;
 }

@@ -52,6 +52,52 @@ __global__ void k_add_leaf(unsigned long long *cell, unsigned long long count)
     if (threadIdx.x == 0 && blockIdx.x == 0) *cell += count;
 }
 
+// Sum of histogram row 1 (leaves with h = 1) into *out: taken before a
+// range walk adds to a caller's histogram, as the base of k_check_paths.
+__global__ void __launch_bounds__(256) k_row1_sum(const unsigned long long *__restrict__ hist, int hstride,
+                                                  unsigned long long *out)
+{
+    __shared__ unsigned long long acc;
+    if (threadIdx.x == 0) acc = 0;
+    __syncthreads();
+    unsigned long long a = 0;
+    for (int p = threadIdx.x; p < hstride; p += blockDim.x) a += hist[hstride + p];
+    atomicAdd(&acc, a);
+    __syncthreads();
+    if (threadIdx.x == 0) *out = acc;
+}
+
+// Consistency of a walk's (h, p) leaf histogram with the root paths of the
+// SCT (Thm. scr).  Each walked root has exactly one all-pivot path, a leaf
+// with h = 1, so row 1 gains one leaf per root (`roots`; minus *base, the
+// row's sum before the walk, if base is set).  With orow set (a walk of every
+// root, kmax >= 2), the 2-cliques read off the histogram,
+// sum_p p * hist[1][p] + sum_p hist[2][p], are the edges of the DAG,
+// orow[n] - orow[0].  A mismatch means walk work was lost or repeated:
+// DERR_CHECK.
+__global__ void __launch_bounds__(256) k_check_paths(const unsigned long long *__restrict__ hist, int hstride,
+                                                     const unsigned long long *base, unsigned long long roots,
+                                                     const int64_t *orow, int64_t n, unsigned *err)
+{
+    __shared__ unsigned long long s1, s2;
+    if (threadIdx.x == 0) s1 = s2 = 0;
+    __syncthreads();
+    unsigned long long a = 0, b = 0;
+    for (int p = threadIdx.x; p < hstride; p += blockDim.x) {
+        const unsigned long long x = hist[hstride + p];
+        a += x;
+        b += x * (unsigned long long)p;
+        if (2 < hstride) b += hist[2 * (size_t)hstride + p];
+    }
+    atomicAdd(&s1, a);
+    atomicAdd(&s2, b);
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    bool ok = s1 - (base ? *base : 0ull) == roots;
+    if (orow) ok = ok && s2 == (unsigned long long)(orow[n] - orow[0]);
+    if (!ok) atomicOr(err, DERR_CHECK);
+}
+
 // Local counts of roots with no out-neighbour: c_1(r) += 1.
 __global__ void k_vertex_trivial(const uint32_t *__restrict__ roots, unsigned nroots,
                                  unsigned long long *cv, int K, int W)
@@ -207,7 +253,7 @@ static pvt_status launch_all(pvt_dag *g, const CountArgs &A0, cudaStream_t s)
         pvt_status st = grow(g->cframes, (size_t)cap * FRAME_WORDS, s);
         if (st != PVT_OK) return st;
         A.emit = g->cframes.p;
-        A.emit_count = g->d_q + 8;
+        A.emit_count = reinterpret_cast<unsigned long long *>(g->d_q + 8);  // words 8..9
         A.emit_cap = cap;
     }
     // heavy classes on side streams so that they overlap the light ones (or
@@ -317,6 +363,12 @@ static pvt_status enqueue_global(pvt_dag *g, int32_t kmax, int32_t W, uint64_t *
     A.stats = g->d_stats;
     if ((st = launch_all<MODE_GLOBAL>(g, A, s)) != PVT_OK) return st;
     phase_begin(g, PH_FINISH, s);
+    if (kmax >= 1) {
+        k_check_paths<<<1, 256, 0, s>>>(g->hist.p, hstride, nullptr, (unsigned long long)g->n,
+                                        kmax >= 2 ? g->orow : nullptr, g->n, g->d_err);
+        PVT_CK(cudaGetLastError());
+        g->stats.launches++;
+    }
     k_combine<<<kmax + 1, 256, 0, s>>>(g->hist.p, hstride, g->binom.p, W, kmax,
                                        reinterpret_cast<unsigned long long *>(C), g->d_err);
     PVT_CK(cudaGetLastError());
@@ -466,6 +518,13 @@ pvt_status count_hist(pvt_dag *g, int64_t begin, int64_t end, int32_t kmax, uint
     PVT_CK(cudaMemsetAsync(g->d_err, 0, sizeof(unsigned), s));
     PVT_CK(cudaMemsetAsync(g->d_q, 0, 16 * sizeof(unsigned), s));
     PVT_CK(cudaMemsetAsync(g->d_stats, 0, 16 * sizeof(unsigned long long), s));
+    // row 1 of the caller's histogram before this range adds to it
+    unsigned long long *row1_base = g->d_stats + 14;
+    if (kmax >= 1) {
+        k_row1_sum<<<1, 256, 0, s>>>(reinterpret_cast<const unsigned long long *>(hist), hstride, row1_base);
+        PVT_CK(cudaGetLastError());
+        g->stats.launches++;
+    }
     if (g->wcnt[0] && kmax >= 1) {
         k_add_leaf<<<1, 32, 0, s>>>(reinterpret_cast<unsigned long long *>(hist) + hstride,
                                     (unsigned long long)g->wcnt[0]);
@@ -483,6 +542,14 @@ pvt_status count_hist(pvt_dag *g, int64_t begin, int64_t end, int32_t kmax, uint
     A.err = g->d_err;
     A.stats = g->d_stats;
     if ((st = launch_all<MODE_GLOBAL>(g, A, s)) != PVT_OK) return st;
+    if (kmax >= 1) {
+        int64_t walked = 0;
+        for (int c = 0; c < NCLASS; ++c) walked += g->wcnt[c];
+        k_check_paths<<<1, 256, 0, s>>>(A.hist, hstride, row1_base, (unsigned long long)walked, nullptr, 0,
+                                        g->d_err);
+        PVT_CK(cudaGetLastError());
+        g->stats.launches++;
+    }
     return end_call(g, s, "pvt_count_hist");
 }
 
@@ -880,6 +947,9 @@ extern "C" pvt_status pvt_count_global_noalloc(int64_t n, const int64_t *orow, c
                         : NWn <= 2 ? launch_noalloc<2>(A, alpha, num_sms, s)
                                    : launch_noalloc<4>(A, alpha, num_sms, s);
         if (st != PVT_OK) return st;
+        k_check_paths<<<1, 256, 0, s>>>(hist, hstride, nullptr, (unsigned long long)n, kmax >= 2 ? orow : nullptr, n,
+                                        err);
+        PVT_CK(cudaGetLastError());
     }
     k_combine<<<kmax + 1, 256, 0, s>>>(hist, hstride, binom, W, kmax, reinterpret_cast<unsigned long long *>(C), err);
     PVT_CK(cudaGetLastError());
@@ -893,6 +963,10 @@ extern "C" pvt_status pvt_count_global_noalloc(int64_t n, const int64_t *orow, c
     if (herr & DERR_OVERFLOW) {
         set_error("pvt_count_global_noalloc: multi-word overflow");
         return PVT_EOVERFLOW;
+    }
+    if (herr & DERR_CHECK) {
+        set_error("pvt_count_global_noalloc: internal consistency check of the root paths failed");
+        return PVT_EINTERNAL;
     }
     if (herr) {
         set_error("pvt_count_global_noalloc: device capacity check failed");

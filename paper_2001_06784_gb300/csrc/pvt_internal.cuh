@@ -28,7 +28,8 @@ enum : unsigned {
     DERR_TIMEOUT = 2u,    // bounded spin-wait gave up
     DERR_OVERFLOW = 4u,   // multi-word arithmetic carried out of the top word
     DERR_RANGE = 8u,      // an index fell outside its table (capacity bug)
-    DERR_NOTSIMPLE = 16u  // CSR validation failed
+    DERR_NOTSIMPLE = 16u,  // CSR validation failed
+    DERR_CHECK = 32u       // a walk's leaf histogram disagrees with its root paths
 };
 
 // Per-call scratch that lives as long as the dag (grown on demand).

@@ -143,7 +143,8 @@ struct CountArgs {
     // two-phase global counts: the wide walk emits every compacted subtree
     // as a frame (layout below) for k_walk_frames; null: walk them in place
     uint32_t *emit;             // [emit_cap][FRAME_WORDS]
-    unsigned *emit_count;       // frames reserved so far (may pass emit_cap)
+    unsigned long long *emit_count;  // compacted subtrees met so far (passes emit_cap once the
+                                     // buffer is full; 64-bit: long walks meet billions)
     unsigned emit_cap;
 };
 
@@ -153,6 +154,9 @@ struct CountArgs {
 // of the frames produced (head > tail), after the slot's previous occupant
 // (ticket t - qcap) has been copied out.  A warp holding a ticket leaves once
 // no item is outstanding: then no warp can produce another frame.
+// Head and tail are 64-bit ticket counters (two words each): a long walk
+// donates billions of frames.  A ring slot stores the low 32 bits of t+1,
+// which tell ticket t from the slot's previous occupant t - qcap.
 constexpr int Q_HEAD = 0, Q_TAIL = 32, Q_OUT = 64, Q_ROOT = 96, QCTL_WORDS = 128;
 // Frame: [0] kind; wide (1): [1] root index, [2] d, [3] (h<<16)|p, [4..4+NW) S;
 // compacted (2): [1] (h<<16)|p, [2] S, [3] out-degree class of the root,
@@ -247,11 +251,19 @@ constexpr unsigned long long SPLIT_IDLE_LIMIT_NS = 120000000000ull;  // 120 s wi
 constexpr unsigned long long SPLIT_SLOT_LIMIT_NS = 2000000000ull;  // 2 s for a ring slot to free up
 
 __device__ __forceinline__ unsigned vload(const unsigned *p) { return *(const volatile unsigned *)p; }
+__device__ __forceinline__ unsigned long long vload64(const uint32_t *p)
+{
+    return *(const volatile unsigned long long *)p;
+}
+__device__ __forceinline__ unsigned long long *qword(uint32_t *p)
+{
+    return reinterpret_cast<unsigned long long *>(p);
+}
 
 // Lane 0: are warps waiting on tickets that no frame fills yet?
 __device__ __forceinline__ bool queue_hungry(const CountArgs &A)
 {
-    return vload(A.qctl + Q_HEAD) > vload(A.qctl + Q_TAIL);
+    return vload64(A.qctl + Q_HEAD) > vload64(A.qctl + Q_TAIL);
 }
 
 // Reserve the slot of the next frame (one more outstanding item); all lanes
@@ -262,9 +274,10 @@ __device__ __forceinline__ uint32_t *frame_reserve(const CountArgs &A, int lane,
     int ok = 1;
     if (lane == 0) {
         atomicAdd(A.qctl + Q_OUT, 1u);
-        t = atomicAdd(A.qctl + Q_TAIL, 1u);
-        if (t >= A.qcap) {
-            const unsigned want = t - A.qcap + 1u, slot = t & (A.qcap - 1u);
+        const unsigned long long t64 = atomicAdd(qword(A.qctl + Q_TAIL), 1ull);
+        t = (unsigned)t64;
+        if (t64 >= A.qcap) {
+            const unsigned want = (unsigned)(t64 - A.qcap + 1u), slot = t & (A.qcap - 1u);
             const unsigned long long t0 = global_ns();
             while (vload(A.qdone + slot) != want) {
                 if (global_ns() - t0 > SPLIT_SLOT_LIMIT_NS) { atomicOr(A.err, DERR_TIMEOUT); ok = 0; break; }
@@ -499,7 +512,7 @@ __device__ void compact_loop(WarpWork<NW> &Wk, unsigned long long *shist, const 
                     }
                     top += nR;
                     __syncwarp();
-                    if (SPLIT && clk.nodes >= clk.next) {
+                    if (SPLIT && (int)(clk.nodes - clk.next) >= 0) {
                         clk.next = clk.nodes + clk.every;
                         // waiting warps get the largest pending work first: the
                         // enclosing wide walk's oldest frame, else our oldest
@@ -598,10 +611,10 @@ __device__ void walk_compact(WarpWork<NW> &Wk, unsigned long long *shist, const 
     const uint32_t r1 = compact_rows<NW>(Wk, lane, S, s);
     const uint32_t S1 = s >= 32 ? FULL : ((1u << s) - 1u);
     if (A.emit) {
-        unsigned i = 0;
-        if (lane == 0) i = atomicAdd(A.emit_count, 1u);
+        unsigned long long i = 0;
+        if (lane == 0) i = atomicAdd(A.emit_count, 1ull);
         i = __shfl_sync(FULL, i, 0);
-        if (i < A.emit_cap) {
+        if (i < (unsigned long long)A.emit_cap) {
             uint32_t *fr = A.emit + (size_t)i * FRAME_WORDS;
             fr[4 + lane] = r1;
             if (lane == 0) {
@@ -867,7 +880,7 @@ __device__ void walk_root(WarpWork<NW> &Wk, unsigned long long *shist, const Cou
                     }
                     top += before;
                     __syncwarp();  // pushed frames visible to every lane
-                    if (SPLIT && clk.nodes >= clk.next) {
+                    if (SPLIT && (int)(clk.nodes - clk.next) >= 0) {
                         clk.next = clk.nodes + clk.every;
                         // donate the oldest pending frame (largest subtree) to an idle warp
                         int ndon = 0;
@@ -955,7 +968,7 @@ __device__ __forceinline__ int queue_take(const CountArgs &A, unsigned nitems, u
     }
     // a ticket for the next donated frame; wait on its own slot
     int kind = 0;
-    const unsigned t = atomicAdd(A.qctl + Q_HEAD, 1u);
+    const unsigned t = (unsigned)atomicAdd(qword(A.qctl + Q_HEAD), 1ull);
     unsigned last_out = 0xFFFFFFFFu, nap = 64;
     unsigned long long t0 = global_ns();
     const unsigned slot = t & (A.qcap - 1u);
@@ -1174,8 +1187,8 @@ __global__ void __launch_bounds__(32 * FRAME_WPB) k_walk_frames(CountArgs A)
     WarpWork<1> *ww = reinterpret_cast<WarpWork<1> *>(smem);
     unsigned long long *shist = reinterpret_cast<unsigned long long *>(ww + FRAME_WPB);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const unsigned emitted = *(volatile unsigned *)A.emit_count;
-    const unsigned nframes = min(emitted, A.emit_cap);
+    const unsigned long long emitted = *(volatile unsigned long long *)A.emit_count;
+    const unsigned nframes = (unsigned)min(emitted, (unsigned long long)A.emit_cap);
     if (blockIdx.x == 0 && threadIdx.x == 0) A.stats[3 + FRAMES_SLOT + 1] = emitted;
     WalkCounters wc;
     if (SHIST) {
@@ -1237,10 +1250,10 @@ __global__ void __launch_bounds__(32 * FRAME_WPB) k_walk_frames(CountArgs A)
 
 // Queue counters of the frame walk: outstanding items = the emitted frames
 // (read on the device: the count is final once the wide walks are done).
-static __global__ void k_frames_init(uint32_t *qctl, const unsigned *emit_count, unsigned cap)
+static __global__ void k_frames_init(uint32_t *qctl, const unsigned long long *emit_count, unsigned cap)
 {
     for (int i = threadIdx.x; i < QCTL_WORDS; i += blockDim.x)
-        qctl[i] = i == Q_OUT ? min(*emit_count, cap) : 0u;
+        qctl[i] = i == Q_OUT ? (unsigned)min(*emit_count, (unsigned long long)cap) : 0u;
 }
 
 // ----------------------------------------------------------- batched form
