@@ -48,6 +48,8 @@ def declare(lib):
     lib.orc_count.argtypes = [i64, vp, vp, i32, i32, vp, vp, vp, vp, i64, i32, vp, vp, i32]
     lib.orc_paths.restype = i64
     lib.orc_paths.argtypes = [i64, vp, vp, vp, i64]
+    lib.orc_triangles.restype = i64
+    lib.orc_triangles.argtypes = [i64, vp, vp, i32]
     return lib
 
 
@@ -147,6 +149,16 @@ def count(row_ptr, col, *, kmax: int = -1, vertex: bool = False, edge: bool = Fa
     if hist_dim:
         out["hist"] = hist
     return out
+
+
+def triangles(row_ptr, col, threads: int = 1) -> int:
+    """Number of triangles (C_3, Sec. 2), by plain enumeration over the
+    (degree, id) order, independent of the SCT walk (orc_triangles)."""
+    row_ptr, col = _csr(row_ptr, col)
+    t = _load().orc_triangles(len(row_ptr) - 1, row_ptr.ctypes.data, col.ctypes.data, int(threads))
+    if t < 0:
+        raise RuntimeError("oracle: triangles: invalid argument or out of memory")
+    return int(t)
 
 
 def frequency(table, k: int) -> dict:

@@ -527,3 +527,90 @@ int64_t orc_paths(int64_t n, const int64_t *rp, const uint32_t *col, int32_t *ou
     graph_free(&g);
     return len;
 }
+
+/*
+ * Triangles: the number of vertex triples that are pairwise adjacent, which
+ * is C_3 of the k-clique counts (Sec. 2, k = 3).  Plain enumeration,
+ * independent of the SCT code above: order the vertices by (degree, id),
+ * keep for every vertex its neighbours later in that order (N+), and count
+ * each triangle once, at its earliest vertex u, as a pair v -> w of N+(u)
+ * with w in N+(v) (the "forward" algorithm of Schank and Wagner, 2005, with
+ * a marker array over N+(u)).  Returns the count, or -1 for bad input or no
+ * memory.
+ */
+static int later(const int64_t *rp, uint32_t a, uint32_t b)
+{
+    const int64_t da = rp[a + 1] - rp[a], db = rp[b + 1] - rp[b];
+    return da < db || (da == db && a < b);
+}
+
+typedef struct {
+    const int64_t *orow;
+    const uint32_t *ocol;
+    int64_t n, *next, count;
+    uint8_t *mark;
+} tri_worker;
+
+static void *tri_main(void *arg)
+{
+    tri_worker *k = (tri_worker *)arg;
+    for (;;) {
+        const int64_t u0 = __atomic_fetch_add(k->next, 64, __ATOMIC_RELAXED);
+        if (u0 >= k->n) break;
+        const int64_t u1 = u0 + 64 < k->n ? u0 + 64 : k->n;
+        for (int64_t u = u0; u < u1; ++u) {
+            for (int64_t i = k->orow[u]; i < k->orow[u + 1]; ++i) k->mark[k->ocol[i]] = 1;
+            for (int64_t i = k->orow[u]; i < k->orow[u + 1]; ++i) {
+                const uint32_t v = k->ocol[i];
+                for (int64_t j = k->orow[v]; j < k->orow[v + 1]; ++j) k->count += k->mark[k->ocol[j]];
+            }
+            for (int64_t i = k->orow[u]; i < k->orow[u + 1]; ++i) k->mark[k->ocol[i]] = 0;
+        }
+    }
+    return NULL;
+}
+
+/* threads >= 1 split the vertices u in chunks of 64 (each thread its own
+ * marker array and count, summed at the end). */
+int64_t orc_triangles(int64_t n, const int64_t *rp, const uint32_t *col, int threads)
+{
+    if (n < 0 || (n > 0 && (!rp || !col)) || threads < 1) return -1;
+    if (n == 0) return 0;
+    int64_t *orow = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n + 1));
+    uint32_t *ocol = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)(rp[n] > 0 ? rp[n] : 1));
+    tri_worker *wk = (tri_worker *)calloc((size_t)threads, sizeof(tri_worker));
+    pthread_t *th = (pthread_t *)calloc((size_t)threads, sizeof(pthread_t));
+    int ok = orow && ocol && wk && th;
+    for (int t = 0; ok && t < threads; ++t) ok = (wk[t].mark = (uint8_t *)calloc((size_t)n, 1)) != NULL;
+    int64_t total = -1;
+    if (ok) {
+        orow[0] = 0;
+        for (int64_t u = 0; u < n; ++u) {
+            int64_t k = orow[u];
+            for (int64_t i = rp[u]; i < rp[u + 1]; ++i)
+                if (later(rp, (uint32_t)u, col[i])) ocol[k++] = col[i];
+            orow[u + 1] = k;
+        }
+        int64_t next = 0;
+        for (int t = 0; t < threads; ++t) {
+            wk[t].orow = orow;
+            wk[t].ocol = ocol;
+            wk[t].n = n;
+            wk[t].next = &next;
+        }
+        if (threads == 1) {
+            tri_main(&wk[0]);
+        } else {
+            for (int t = 0; t < threads; ++t) pthread_create(&th[t], NULL, tri_main, &wk[t]);
+            for (int t = 0; t < threads; ++t) pthread_join(th[t], NULL);
+        }
+        total = 0;
+        for (int t = 0; t < threads; ++t) total += wk[t].count;
+    }
+    for (int t = 0; wk && t < threads; ++t) free(wk[t].mark);
+    free(wk);
+    free(th);
+    free(orow);
+    free(ocol);
+    return total;
+}

@@ -222,6 +222,21 @@ def test_workload_full_global(pvt, name):
     assert got[1] == n and got[2] == m
 
 
+def test_workload_cl3m_truncated(pvt):
+    """The 128M-edge com-orkut-shaped graph (degeneracy 733), truncated to
+    k <= 3 (Sec. 4, counting for a specific k): its all-k tree (about 1.6e12
+    nodes) is far beyond the oracle, but C_1 = n, C_2 = m and C_3 equals the
+    oracle's triangle enumeration, at full size, word for word."""
+    rp, col = graphgen.workload("cl3m_m117m_b2.0_comm2000")
+    n, m = len(rp) - 1, len(col) // 2
+    T = oracle.triangles(rp, col, threads=os.cpu_count() or 1)
+    dag = gpu_dag(pvt, rp, col, validate=False)
+    assert dag.alpha == 733
+    C = pvt.to_ints(dag.count_global(kmax=3))
+    assert C == [0, n, m, T]
+    dag.free()
+
+
 @pytest.mark.parametrize("make", [
     lambda: graphs.complete(40), lambda: graphs.multipartite([3, 5, 7, 2]), lambda: graphs.gnp(300, 0.1, 3),
     lambda: graphgen.from_edges(5, []), lambda: graphs.disjoint_cliques([1, 2, 33, 70]),

@@ -168,6 +168,42 @@ def test_triangles_from_adjacency_powers(kind):
     assert [row[3] for row in ce] == [int(round(A2[u, v])) for u, v in edges]
 
 
+# oracle.triangles: a second, SCT-free route to C_3 (used at full size)
+
+@pytest.mark.parametrize("kind", ["gnp", "er2k", "planted"])
+def test_triangle_enumeration_pins(kind):
+    """orc_triangles equals trace(A^3)/6 and the SCT oracle's C_3, for one
+    thread and several."""
+    if kind == "gnp":
+        rp, col = graphs.gnp(250, 0.08, 5)
+    elif kind == "er2k":
+        rp, col = graphgen.workload("er2k_d20_clique30")
+    else:
+        rp, col = graphgen.generate(400, er_avg_deg=6.0, planted=[(3, 10, 25, 0.8)], seed=9)
+    n = len(rp) - 1
+    A = np.zeros((n, n))
+    src = np.repeat(np.arange(n), np.diff(rp))
+    A[src, col.astype(np.int64)] = 1.0
+    trace = int(round(np.einsum("ij,jk,ki->", A, A, A) / 6))
+    t1, t4 = oracle.triangles(rp, col), oracle.triangles(rp, col, threads=4)
+    assert t1 == t4 == trace == oracle.count(rp, col, kmax=3)["C"][3]
+
+
+@pytest.mark.parametrize("n", [0, 1, 2, 3, 5, 17, 64])
+def test_triangle_enumeration_closed_forms(n):
+    """C(n, 3) on K_n, and disjoint cliques add up; no triangle in a star or
+    a complete bipartite graph."""
+    rp, col = graphs.complete(n)
+    assert oracle.triangles(rp, col) == math.comb(n, 3)
+    sizes = [n, 4, 3, 1]
+    rp, col = graphs.disjoint_cliques(sizes)
+    assert oracle.triangles(rp, col, threads=3) == sum(math.comb(s, 3) for s in sizes)
+    rp, col = graphs.multipartite([1, n + 1])
+    assert oracle.triangles(rp, col) == 0
+    rp, col = graphs.multipartite([n + 2, 7])
+    assert oracle.triangles(rp, col) == 0
+
+
 def test_local_sum_identities():
     rp, col = graphgen.generate(600, er_avg_deg=9.0, planted=[(4, 8, 20, 1.0), (2, 15, 25, 0.85)], seed=21)
     n, m = len(rp) - 1, len(col) // 2
