@@ -84,3 +84,50 @@ def test_mutation_is_caught(name, monkeypatch):
         subprocess.check_call(["gcc", "-O1", "-fPIC", "-shared", "-std=c11", "-pthread", c, "-o", so])
         monkeypatch.setattr(oracle, "_lib", oracle.declare(ctypes.CDLL(so)))
         assert not pins_pass(), f"planted mistake {name!r} went unnoticed"
+
+
+# the SCT-free triangle enumeration has pins of its own
+TRI_MUTATIONS = {
+    "no orientation filter": ("if (later(rp, (uint32_t)u, col[i])) ocol[k++] = col[i];", "ocol[k++] = col[i];"),
+    "marker left set": ("for (int64_t i = k->orow[u]; i < k->orow[u + 1]; ++i) k->mark[k->ocol[i]] = 0;",
+                        "(void)0;"),
+    "chunk end short": ("const int64_t u1 = u0 + 64 < k->n ? u0 + 64 : k->n;",
+                        "const int64_t u1 = u0 + 63 < k->n ? u0 + 63 : k->n;"),
+}
+
+
+def triangle_pins_pass() -> bool:
+    """C(n, 3) on complete graphs and trace(A^3)/6 on random graphs, for one
+    thread and several; False as soon as one fails."""
+    import numpy as np
+    for n in (3, 9, 70):
+        rp, col = graphs.complete(n)
+        if oracle.triangles(rp, col) != math.comb(n, 3) or oracle.triangles(rp, col, threads=3) != math.comb(n, 3):
+            return False
+    for make in (lambda: graphs.gnp(120, 0.1, 4), lambda: graphgen.workload("er2k_d20_clique30")):
+        rp, col = make()
+        n = len(rp) - 1
+        A = np.zeros((n, n))
+        A[np.repeat(np.arange(n), np.diff(rp)), col.astype(np.int64)] = 1.0
+        want = int(round(np.einsum("ij,jk,ki->", A, A, A) / 6))
+        if oracle.triangles(rp, col) != want or oracle.triangles(rp, col, threads=4) != want:
+            return False
+    return True
+
+
+def test_unmutated_triangles_pass():
+    assert triangle_pins_pass()
+
+
+@pytest.mark.parametrize("name", sorted(TRI_MUTATIONS))
+def test_triangle_mutation_is_caught(name, monkeypatch):
+    old, new = TRI_MUTATIONS[name]
+    src = open(SRC).read()
+    assert src.count(old) == 1, f"mutation anchor for {name!r} not unique"
+    with tempfile.TemporaryDirectory() as d:
+        c = os.path.join(d, "mut.c")
+        so = os.path.join(d, "libmut.so")
+        open(c, "w").write(src.replace(old, new))
+        subprocess.check_call(["gcc", "-O1", "-fPIC", "-shared", "-std=c11", "-pthread", c, "-o", so])
+        monkeypatch.setattr(oracle, "_lib", oracle.declare(ctypes.CDLL(so)))
+        assert not triangle_pins_pass(), f"planted mistake {name!r} went unnoticed"
