@@ -217,6 +217,19 @@ pvt_status pvt_dag_stats(const pvt_dag *dag, pvt_stats *out);
 pvt_status pvt_dag_set_profiling(pvt_dag *dag, int32_t enable);
 
 /*
+ * The measured integer ceiling of the walk kernels (no counterpart in the
+ * paper): how many 32-bit AND + population count + add triples -- one pivot
+ * word pair of the walk (Alg. 1 pivot step, |N(S,u)| word by word) -- the
+ * current device sustains per second on independent register chains with
+ * every SM busy (fastest of three timed launches after one warm-up, tens of
+ * milliseconds each).  The roofline of the walk kernels divides by it.
+ *   pairs_per_s  host: receives the rate
+ *   stream       CUDA stream (NULL: the default stream); the call waits for it
+ * Errors: PVT_EINVAL (NULL pairs_per_s), PVT_ECUDA.
+ */
+pvt_status pvt_measure_popc_rate(double *pairs_per_s, void *stream);
+
+/*
  * Launch policy of the walk kernels (no counterpart in the paper, whose
  * parallel variant gives each thread whole roots, Sec. 4 "Parallel version").
  *   persistent  1 (default): per out-degree class, a grid sized to the GPU

@@ -282,6 +282,16 @@ def local_distribution(table: torch.Tensor, k: int, stream=None):
     return values[:nd.value], counts[:nd.value]
 
 
+def measure_popc_rate(device="cuda:0", stream=None):
+    """AND + population count + add triples per second that the device
+    sustains (pvt_measure_popc_rate): the walk kernels' roofline peak."""
+    rate = ctypes.c_double()
+    dev = torch.device(device)
+    with torch.cuda.device(dev):
+        _lib.check(_lib.lib().pvt_measure_popc_rate(ctypes.byref(rate), _stream_handle(stream, dev)))
+    return rate.value
+
+
 def to_ints(t):
     """Word tensor [..., W] (64-bit little-endian words) -> nested lists of
     Python ints."""

@@ -47,7 +47,7 @@ EXPORTS = ("pvt_orient", "pvt_dag_info", "pvt_dag_cores", "pvt_local_distributio
            "pvt_dag_get_policy", "pvt_dag_autotune",
            "pvt_count_global_noalloc", "pvt_server_create", "pvt_server_submit", "pvt_server_wait",
            "pvt_server_result", "pvt_server_destroy", "pvt_dag_free",
-           "pvt_last_error")
+           "pvt_last_error", "pvt_measure_popc_rate")
 
 
 class PivoterError(RuntimeError):
@@ -66,6 +66,8 @@ def load(path: str = LIB_PATH):
     lib.pvt_dag_info.restype = i32
     lib.pvt_dag_info.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(i32),
                                  ctypes.POINTER(i32)]
+    lib.pvt_measure_popc_rate.restype = i32
+    lib.pvt_measure_popc_rate.argtypes = [ctypes.POINTER(ctypes.c_double), vp]
     lib.pvt_count_hist.restype = i32
     lib.pvt_count_hist.argtypes = [vp, i64, i64, i32, vp, vp]
     lib.pvt_combine_hist.restype = i32

@@ -222,6 +222,16 @@ def test_workload_full_global(pvt, name):
     assert got[1] == n and got[2] == m
 
 
+def test_measure_popc_rate(pvt):
+    """The measured AND+POPC+ADD ceiling (the walk roofline's peak) is
+    positive, below 32 triples per SM per clock at 2.2 GHz, and repeatable."""
+    import torch
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    a, b = pvt.measure_popc_rate("cuda:0"), pvt.measure_popc_rate("cuda:0")
+    assert 0 < a < 32 * sms * 2.2e9 and 0 < b < 32 * sms * 2.2e9
+    assert abs(a - b) <= 0.1 * max(a, b)
+
+
 def test_workload_cl3m_truncated(pvt):
     """The 128M-edge com-orkut-shaped graph (degeneracy 733), truncated to
     k <= 3 (Sec. 4, counting for a specific k): its all-k tree (about 1.6e12
