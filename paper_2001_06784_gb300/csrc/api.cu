@@ -229,6 +229,7 @@ extern "C" {
 pvt_status pvt_orient(int64_t n, int64_t nnz, const int64_t *row_ptr, const uint32_t *col,
                       uint32_t flags, void *stream, pvt_dag **dag_out, int32_t *alpha_out)
 {
+    const HostRange range("pvt_orient");
     if (!dag_out || n < 0 || n > 0xFFFFFFFEll || nnz < 0 || (nnz & 1) || (n > 0 && !row_ptr) ||
         (nnz > 0 && !col) || (flags & ~(PVT_VALIDATE | PVT_PROFILE))) {
         set_error("pvt_orient: invalid argument");
@@ -300,27 +301,32 @@ pvt_status pvt_dag_cores(const pvt_dag *dag, uint32_t *core, void *stream)
 
 pvt_status pvt_count_global(pvt_dag *dag, int32_t kmax, int32_t W, uint64_t *C, void *stream)
 {
+    const HostRange range("pvt_count_global");
     return count_global(dag, kmax, W, C, (cudaStream_t)stream);
 }
 
 pvt_status pvt_count_local_vertex(pvt_dag *dag, int32_t kmax, int32_t W, uint64_t *cv, void *stream)
 {
+    const HostRange range("pvt_count_local_vertex");
     return count_local(dag, kmax, W, cv, false, (cudaStream_t)stream);
 }
 
 pvt_status pvt_count_local_edge(pvt_dag *dag, int32_t kmax, int32_t W, uint64_t *ce, void *stream)
 {
+    const HostRange range("pvt_count_local_edge");
     return count_local(dag, kmax, W, ce, true, (cudaStream_t)stream);
 }
 
 pvt_status pvt_count_hist(pvt_dag *dag, int64_t begin, int64_t end, int32_t kmax, uint64_t *hist, void *stream)
 {
+    const HostRange range("pvt_count_hist");
     return count_hist(dag, begin, end, kmax, hist, (cudaStream_t)stream);
 }
 
 pvt_status pvt_combine_hist(pvt_dag *dag, const uint64_t *hist, int32_t kmax, int32_t W, uint64_t *C,
                             void *stream)
 {
+    const HostRange range("pvt_combine_hist");
     return combine_hist(dag, hist, kmax, W, C, (cudaStream_t)stream);
 }
 
@@ -380,6 +386,7 @@ pvt_status pvt_dag_get_policy(const pvt_dag *dag, pvt_policy *out)
 pvt_status pvt_dag_autotune(pvt_dag *dag, int32_t kmax, int32_t W, uint64_t *C, void *stream,
                             pvt_policy *chosen, float *ms)
 {
+    const HostRange range("pvt_dag_autotune");
     return autotune(dag, kmax, W, C, (cudaStream_t)stream, chosen, ms);
 }
 

@@ -876,6 +876,7 @@ extern "C" pvt_status pvt_count_global_noalloc(int64_t n, const int64_t *orow, c
                                                int32_t alpha, int32_t kmax, int32_t W, uint64_t *C,
                                                void *stream)
 {
+    const pvt::HostRange range("pvt_count_global_noalloc");
     using namespace pvt;
     if (n < 0 || n > 0xFFFFFFFEll || (n > 0 && !orow) || !C || kmax < 0 || alpha < 0 || W < 1) {
         set_error("pvt_count_global_noalloc: invalid argument");

@@ -102,6 +102,7 @@ extern "C" pvt_status pvt_local_distribution(const uint64_t *table, int64_t rows
                                              uint64_t *values, uint64_t *counts, int64_t *n_distinct,
                                              void *stream)
 {
+    const pvt::HostRange range("pvt_local_distribution");
     if (rows < 0 || rows > 0xFFFFFFFEll || K < 1 || k < 0 || k >= K || W < 1 || W > WMAX || !n_distinct ||
         (rows > 0 && (!table || !values || !counts))) {
         set_error("pvt_local_distribution: invalid argument");

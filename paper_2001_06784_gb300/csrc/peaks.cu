@@ -47,6 +47,7 @@ __global__ void __launch_bounds__(RATE_THREADS) k_popc_rate(unsigned *sink, int 
 extern "C" pvt_status pvt_measure_popc_rate(double *pairs_per_s, void *stream)
 {
     using namespace pvt;
+    const HostRange range("pvt_measure_popc_rate");
     if (!pairs_per_s) {
         set_error("pvt_measure_popc_rate: NULL argument");
         return PVT_EINVAL;

@@ -1,6 +1,7 @@
 // Internal definitions shared by the CUDA translation units of libpivoter.
 #pragma once
 
+#include <nvtx3/nvToolsExt.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -174,6 +175,16 @@ void stats_reset(pvt_dag *g);
 
 // Read the device status word (synchronises s) and map it to a status.
 pvt_status check_device(pvt_dag *g, cudaStream_t s, const char *what);
+
+// A named host range around a library call, so that a profiler's timeline
+// shows where each call begins and ends (NVTX; nothing happens without an
+// attached tool).
+struct HostRange {
+    explicit HostRange(const char *name) { nvtxRangePushA(name); }
+    ~HostRange() { nvtxRangePop(); }
+    HostRange(const HostRange &) = delete;
+    HostRange &operator=(const HostRange &) = delete;
+};
 
 // Nanosecond clock for bounded waits.
 __device__ __forceinline__ unsigned long long global_ns()
