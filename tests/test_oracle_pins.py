@@ -371,3 +371,20 @@ def test_frequency_bruteforce(n, p, seed):
         assert sum(fv.values()) == n and sum(fe.values()) == m
         assert sum(b * c for b, c in fv.items()) == k * r["C"][k]
         assert sum(b * c for b, c in fe.items()) == math.comb(k, 2) * r["C"][k]
+
+
+@pytest.mark.parametrize("make", [lambda: graphs.complete(12), lambda: graphs.gnp(200, 0.07, 8),
+                                  lambda: graphs.disjoint_cliques([1, 5, 9]),
+                                  lambda: graphgen.workload("er2k_d20_clique30")])
+def test_path_histogram_invariants(make):
+    """The invariants the device checks after every walk, on the oracle's
+    (h, p) leaf histogram: each root has exactly one all-pivot path (row
+    h = 1 sums to n), and the 2-cliques read off rows 1 and 2,
+    sum_p p * hist[1][p] + sum_p hist[2][p], are the m edges."""
+    rp, col = make()
+    n, m = len(rp) - 1, len(col) // 2
+    r = oracle.count(rp, col, hist_dim=0)
+    H = r["alpha"] + 2
+    hist = oracle.count(rp, col, hist_dim=H)["hist"].astype(np.int64)
+    assert int(hist[1].sum()) == n
+    assert int((np.arange(H) * hist[1]).sum() + (hist[2].sum() if H > 2 else 0)) == m
