@@ -42,6 +42,11 @@ MUTATIONS = {
                                   "if (!A[(size_t)pi * s + j] && (j != pi || 1)) R[r++] = j;"),
     "pascal term": ("big_add(row + (size_t)b * nl, prev + (size_t)b * nl, nl, ovf);",
                     "big_add(row + (size_t)b * nl, prev + (size_t)(b - 1) * nl, nl, ovf);"),
+    # root-parallel mode (Sec. 4, "Parallel version"): a chunk that ends one
+    # root short, and a thread's private counts left out of the final sum
+    "root chunk end short": ("int64_t i1 = i0 + 16 < k->nroots ? i0 + 16 : k->nroots;",
+                             "int64_t i1 = i0 + 15 < k->nroots ? i0 + 15 : k->nroots;"),
+    "thread counts not merged": ("if (C && w->C)\n", "if (C && w->C && t == 0)\n"),
 }
 
 
@@ -65,6 +70,28 @@ def pins_pass() -> bool:
                 return False
     except RuntimeError:
         return False
+    return threaded_pins_pass()
+
+
+def threaded_pins_pass() -> bool:
+    """The root-parallel oracle against closed forms and the sequential
+    oracle: C_1 = n, C_2 = m, sums of C(a, k) over disjoint cliques, and
+    t threads equal to one.  Twelve thousand roots in chunks of 16 keep every
+    thread busy, so a thread whose counts are dropped changes the sum."""
+    sizes = [1, 2, 3, 5, 8, 13, 21, 30]
+    rp, col = graphs.disjoint_cliques(sizes)
+    for t in (1, 3):
+        r = oracle.count(rp, col, threads=t)
+        if r["C"] != [0] + [sum(math.comb(a, k) for a in sizes) for k in range(1, r["kmax"] + 1)]:
+            return False
+    rp, col = graphgen.generate(12021, er_avg_deg=10.0, planted=[(6, 12, 20, 1.0), (1, 25, 25, 0.9)], seed=31)
+    n, m = len(rp) - 1, len(col) // 2
+    one = oracle.count(rp, col)
+    if one["C"][1] != n or one["C"][2] != m:
+        return False
+    for t in (2, 7):
+        if oracle.count(rp, col, threads=t)["C"] != one["C"]:
+            return False
     return True
 
 

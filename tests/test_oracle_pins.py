@@ -388,3 +388,52 @@ def test_path_histogram_invariants(make):
     hist = oracle.count(rp, col, hist_dim=H)["hist"].astype(np.int64)
     assert int(hist[1].sum()) == n
     assert int((np.arange(H) * hist[1]).sum() + (hist[2].sum() if H > 2 else 0)) == m
+
+
+# ------------------------------------------ root-parallel mode (Sec. 4, "Parallel version")
+
+def threaded_cases():
+    """Graphs whose root counts are not multiples of the oracle's 16-root
+    chunks, from a brute-force size to a few thousand roots."""
+    return [("gnp37", graphs.gnp(37, 0.45, 9)),
+            ("cliques83", graphs.disjoint_cliques([1, 2, 3, 5, 8, 13, 21, 30])),
+            ("planted2021", graphgen.generate(2021, er_avg_deg=10.0, planted=[(3, 12, 20, 1.0), (1, 25, 25, 0.9)],
+                                              seed=31))]
+
+
+@pytest.mark.parametrize("idx", [0, 1, 2])
+def test_root_parallel_equals_sequential(idx):
+    """The root-parallel oracle (roots in chunks of 16 over t threads, private
+    counts summed at the end) gives the sequential oracle's counts, SCT
+    statistics and (h, p) histogram for t = 2, 3, 7, and C_1 = n, C_2 = m."""
+    name, (rp, col) = threaded_cases()[idx]
+    n, m = len(rp) - 1, len(col) // 2
+    H = oracle.orient(rp, col)[2] + 2
+    one = oracle.count(rp, col, hist_dim=H)
+    assert one["C"][1] == n and one["C"][2] == m
+    if n <= 40:
+        assert one["C"] == brute_counts(rp, col, one["kmax"])[0]
+    if name == "cliques83":
+        sizes = [1, 2, 3, 5, 8, 13, 21, 30]
+        assert one["C"] == [0] + [sum(math.comb(a, k) for a in sizes) for k in range(1, one["kmax"] + 1)]
+    for t in (2, 3, 7):
+        r = oracle.count(rp, col, threads=t, hist_dim=H)
+        assert r["C"] == one["C"], (name, t)
+        assert (r["nodes"], r["leaves"], r["sum_s"]) == (one["nodes"], one["leaves"], one["sum_s"]), (name, t)
+        assert np.array_equal(r["hist"], one["hist"]), (name, t)
+
+
+def test_root_parallel_ranges_add_up():
+    """Disjoint root sets counted with several threads add up to the whole
+    count (roots are independent subproblems, Sec. 4)."""
+    rp, col = threaded_cases()[2][1]
+    n = len(rp) - 1
+    whole = oracle.count(rp, col)
+    perm = np.random.default_rng(4).permutation(n)
+    parts = [np.sort(perm[:701]), np.sort(perm[701:1500]), np.sort(perm[1500:])]
+    total = [0] * len(whole["C"])
+    for i, roots in enumerate(parts):
+        r = oracle.count(rp, col, kmax=whole["kmax"], roots=roots, threads=2 + i)
+        assert r["C"][1] == len(roots)
+        total = [a + b for a, b in zip(total, r["C"])]
+    assert total == whole["C"]
