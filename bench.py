@@ -31,10 +31,11 @@ L2_FLUSH_BYTES = 256 << 20   # > 129 MB L2
 POPC_PER_CLK_PER_SM = 16     # 32-bit population count issue rate per SM per clock
 SM_COUNT = 152
 SM_MAX_MHZ = 2070.0
-# DRAM bytes (read + write) per launch of the walk kernels, from the ncu
-# captures summarised under profiles/; an entry must be removed whenever its
-# kernel changes, so that the bench line reports null instead of a stale figure
-NCU_DRAM_BYTES = {"walk_frames": 331112192 + 3017984}
+# DRAM bytes (read + write) per launch of a kernel, from an ncu capture of the
+# kernel as it is now (summarised under profiles/, with the capture's date);
+# an entry is removed whenever its kernel changes, so that the bench line
+# reports null instead of a stale figure
+NCU_DRAM_BYTES = {}
 
 
 def parse():
@@ -45,6 +46,7 @@ def parse():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-sequential", action="store_true", help="skip the one-core oracle run of the CPU baseline")
     ap.add_argument("--no-local", action="store_true", help="skip the per-vertex / per-edge measurement")
     ap.add_argument("--serving-queries", type=int, default=300,
                     help="queries in the serving stream (the full stream is 10000); 0 skips serving")
@@ -125,9 +127,35 @@ def whole_job_rate(units_per_rank: float, world: int, seconds_max: float) -> flo
     return world * units_per_rank / seconds_max
 
 
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu), for the baseline's context."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+def min_words(n: int, alpha: int) -> int:
+    """64-bit words that hold every count: each is at most n * 2^alpha."""
+    return max(1, (int(n).bit_length() + alpha + 1 + 63) // 64)
+
+
+def workload_config(name, n, m, alpha, omega):
+    """The `config` of both arms: the workload and what it fixes."""
+    return {"workload": name, "n": n, "m": m, "alpha": alpha, "omega": omega, "kmax": alpha + 1,
+            "W": min_words(n, alpha), "counts": "global C_k, every k",
+            "l2": "GPU arm: a 256 MiB write flushes the 129 MB L2 between timed steps"}
+
+
 def run_reference(args, ws, rank):
-    """The CPU oracle as the reference arm: each step walks a uniform random
-    quarter of the roots on every host core; edges/s = m * fraction / time."""
+    """The CPU oracle as the reference arm: every step counts the whole
+    workload with the root-parallel oracle (one thread per host core, the
+    paper's parallel scheme); edges/s = m / step time."""
     if rank != 0:
         return
     import oracle
@@ -135,24 +163,24 @@ def run_reference(args, ws, rank):
     rp, col = graphgen.workload(args.workload)
     n, m = len(rp) - 1, len(col) // 2
     cores = os.cpu_count() or 1
-    frac = 0.25
-    rng = np.random.default_rng(12345)
-    times = []
+    _, _, alpha = oracle.orient(rp, col)
+    times, C = [], None
     for i in range(args.warmup + args.steps):
-        roots = np.sort(rng.choice(n, int(n * frac), replace=False)).astype(np.uint32)
         t0 = time.perf_counter()
-        oracle.count(rp, col, roots=roots, threads=cores)
+        C = oracle.count(rp, col, kmax=alpha + 1, threads=cores)["C"]
         dt = time.perf_counter() - t0
         if i >= args.warmup:
             times.append(dt)
     t = float(np.mean(times))
-    value = m * frac / t
-    sample = f"uniform random {frac:.0%} of the roots per step (all host cores); full-graph time estimated as t/{frac}"
+    value = m / t
+    omega = max(k for k, c in enumerate(C) if c)
+    sample = "whole workload every step (root-parallel oracle, one thread per host core)"
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": "edges/s", "n_gpus": args.gpus,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1000.0, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "u32 limbs (exact)", "data": "synthetic",
-           "config": {"workload": args.workload, "n": n, "m": m},
-           "cpu_baseline": {"value": value, "unit": "edges/s", "cores": cores, "kind": "oracle", "sample": sample},
+           "config": workload_config(args.workload, n, m, alpha, omega),
+           "cpu_baseline": {"value": value, "unit": "edges/s", "cores": cores, "cpu": cpu_model(), "kind": "oracle",
+                            "sample": sample},
            "e2e": {"value": value, "unit": "edges/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
 
@@ -506,12 +534,11 @@ def main():
     out = {"metric": METRIC, "value": value, "unit": "edges/s", "n_gpus": ws, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "u64 words (exact integers)", "data": "synthetic",
-           "config": {"workload": args.workload, "n": n, "m": m, "alpha": alpha, "omega": omega, "kmax": kmax,
-                      "W": W, "form": "persistent work queue", "l2": "flushed (256 MiB write) between steps",
-                      "policy": step_policy,
-                      "autotune_ms": {c: [round(float(x), 3) for x in tune_ms[i]]
-                                      for i, c in enumerate(("chunk4_split", "chunk1_nosplit", "chunk16_split"))},
-                      "parallelism": "replicas" if ws > 1 else "single"},
+           "config": workload_config(args.workload, n, m, alpha, omega),
+           "run": {"form": "persistent work queue", "policy": step_policy,
+                   "autotune_ms": {c: [round(float(x), 3) for x in tune_ms[i]]
+                                   for i, c in enumerate(("chunk4_split", "chunk1_nosplit", "chunk16_split"))},
+                   "parallelism": "replicas" if ws > 1 else "single"},
            "roofline": roofline,
            "e2e": {"value": e2e_value, "unit": "edges/s", "ms_per_step": e2e_s * 1000.0 / len(e2e_ms),
                    "h2d_bytes_per_step": int(rp_h.numel() * 8 + col_h.numel() * 4),
@@ -538,7 +565,8 @@ def main():
     if rank == 0 and args.serving_queries > 0:
         out["serving"] = run_serving(args, dev)
 
-    # ---- CPU baseline: the oracle, whole workload, every host core; also
+    # ---- CPU baseline: the oracle, whole workload, every host core (the
+    # paper's parallel scheme) and one core (its sequential form); also
     # confirms this run's counts bit-exactly
     if rank == 0 and not args.no_cpu_baseline:
         import oracle
@@ -546,8 +574,16 @@ def main():
         t0 = time.perf_counter()
         ref = oracle.count(rp_np, col_np, kmax=kmax, threads=cores)
         dt = time.perf_counter() - t0
-        out["cpu_baseline"] = {"value": m / dt, "unit": "edges/s", "cores": cores, "kind": "oracle",
-                               "sample": "whole workload, root-parallel oracle, one run", "seconds": dt}
+        seq = None
+        if not args.no_sequential:
+            t0 = time.perf_counter()
+            ref1 = oracle.count(rp_np, col_np, kmax=kmax, threads=1)
+            dt1 = time.perf_counter() - t0
+            seq = {"value": m / dt1, "unit": "edges/s", "cores": 1, "seconds": dt1,
+                   "sample": "whole workload, sequential oracle, one run", "parity": ref1["C"] == C_ints}
+        out["cpu_baseline"] = {"value": m / dt, "unit": "edges/s", "cores": cores, "cpu": cpu_model(),
+                               "kind": "oracle", "sample": "whole workload, root-parallel oracle, one run",
+                               "seconds": dt, "sequential": seq}
         out["parity"] = "bit-exact" if ref["C"] == C_ints else "MISMATCH"
     if rank == 0:
         print(json.dumps(out), flush=True)

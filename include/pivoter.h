@@ -185,9 +185,10 @@ pvt_status pvt_local_distribution(const uint64_t *table, int64_t rows, int32_t K
 /*
  * Statistics of the last orient or count call on a dag (no counterpart in
  * the paper's algorithms; its Fig. treesize reports SCT sizes).  Tree
- * figures are of the walk the device performed: nodes popped from the DFS
- * stacks (leaves included; a node whose label is a clique is closed as one
- * leaf), root-to-leaf paths, and the bitset words ANDed and popcounted in
+ * figures are of the walk the device performed: nodes visited (leaves and
+ * roots with no out-neighbour included; a node whose label is a nonempty
+ * clique is closed as one leaf, so the |S| nodes of its pivot chain are not
+ * visited), root-to-leaf paths, and the bitset words ANDed and popcounted in
  * pivot selection (|S| * ceil(d/32) per internal node).  ms[] holds device
  * time per phase when profiling is on (else zeros): [0] peel, [1] orient
  * (DAG CSR and root classes), [2..7] the walk kernels of out-degree classes
@@ -212,6 +213,29 @@ typedef struct pvt_stats {
 
 /* Copy the statistics of the last call into *out (host). */
 pvt_status pvt_dag_stats(const pvt_dag *dag, pvt_stats *out);
+
+/*
+ * Depth profile of the SCT (no counterpart in the paper's algorithms; its
+ * Fig. treesize reports SCT sizes): the leaves walked by the last completed
+ * pvt_count_global on this dag by depth d = h + p, the number of links on
+ * the root-to-leaf path (= the size of the largest clique the path encodes,
+ * H(T) with all of P(T)), for d = 0..alpha+1.
+ *   depth   host uint64[alpha + 2]
+ * Errors: PVT_EINVAL (NULL argument, or no completed global count since
+ * pvt_orient), PVT_ECUDA.  The call synchronises `stream`.
+ */
+pvt_status pvt_dag_leaf_depths(pvt_dag *dag, uint64_t *depth, void *stream);
+
+/*
+ * The orientation itself (Lemma degen; Alg. 1 step 1): the DAG's out-lists
+ * N+(v), v = 0..n-1, each sorted by vertex id -- the roots' children whose
+ * subtrees the count calls walk.
+ *   orow   device int64[n + 1] (caller-owned), CSR row offsets
+ *   ocol   device uint32[m] (caller-owned; may be NULL when m = 0)
+ * Errors: PVT_EINVAL (NULL argument), PVT_ECUDA.  The call synchronises
+ * `stream`.
+ */
+pvt_status pvt_dag_out_lists(const pvt_dag *dag, int64_t *orow, uint32_t *ocol, void *stream);
 
 /* Enable (1) or disable (0) per-phase device timing with CUDA events. */
 pvt_status pvt_dag_set_profiling(pvt_dag *dag, int32_t enable);
@@ -256,6 +280,13 @@ pvt_status pvt_measure_popc_rate(double *pairs_per_s, void *stream);
  *               replays it at later calls with the same three (the dag's
  *               buffers are fixed after orientation); 0 (default): launch
  *               directly.  Replayed calls report no phase times.
+ *   wait_limit_us  0 (default): the bounded device-side waits of the walk
+ *               (an idle warp waiting for a donated frame, a donor waiting
+ *               for a free ring slot) give up after 120 s without progress
+ *               and 2 s respectively; > 0: after this many microseconds
+ *               instead.  A wait that gives up ends the call with
+ *               PVT_ETIMEOUT and leaves the library usable; the field
+ *               exists to exercise that path (0 .. 10^9).
  * Each field is checked: PVT_EINVAL for a value out of range.
  */
 typedef struct pvt_policy {
@@ -264,6 +295,7 @@ typedef struct pvt_policy {
     int32_t split[7];
     int32_t graph;
     int32_t frames;
+    int32_t wait_limit_us;
 } pvt_policy;
 
 /* Set the launch policy for later count calls on this dag (drops a recorded
@@ -308,12 +340,17 @@ pvt_status pvt_dag_autotune(pvt_dag *dag, int32_t kmax, int32_t W, uint64_t *C, 
  *                list longer than alpha is refused with PVT_EINVAL)
  *   kmax, W, C   as pvt_count_global; W at most 4 (else PVT_EINVAL)
  * The first call on a device looks up the array's device address with that
- * device current; make that first call before any stream capture.  Every
- * call on a device shares the one array and clears what must start at zero;
- * calls whose work overlaps on the GPU (other streams, other host threads)
- * race on it and must be serialised by the caller.  The call returns once C
- * is complete and checked (the root-path checks of pvt_count_global, every
- * vertex being a root; PVT_EINTERNAL if they fail).
+ * device current.  Every call on a device shares the one array and clears
+ * what must start at zero; calls whose work overlaps on the GPU (other
+ * streams, other host threads) race on it and must be serialised by the
+ * caller.  The call reads its status word back and synchronises `stream`
+ * before it returns, so it cannot be called while `stream` is being
+ * captured into a CUDA graph.  It returns once C is complete and checked
+ * (the root-path checks of pvt_count_global, every vertex being a root;
+ * PVT_EINTERNAL if they fail).
+ * Errors: PVT_EINVAL (NULL orow or ocol with n > 0, NULL C, alpha or W
+ * beyond the limits above, an out-list longer than alpha), PVT_EOVERFLOW,
+ * PVT_ECUDA, PVT_EINTERNAL.
  */
 pvt_status pvt_count_global_noalloc(int64_t n, const int64_t *orow, const uint32_t *ocol, int32_t alpha,
                                     int32_t kmax, int32_t W, uint64_t *C, void *stream);

@@ -45,7 +45,7 @@ def declare(lib):
     lib.orc_orient.restype = i32
     lib.orc_orient.argtypes = [i64, vp, vp, vp, vp, vp]
     lib.orc_count.restype = i32
-    lib.orc_count.argtypes = [i64, vp, vp, i32, i32, vp, vp, vp, vp, i64, i32, vp, vp, i32]
+    lib.orc_count.argtypes = [i64, vp, vp, i32, i32, vp, vp, vp, vp, i64, i32, vp, vp, i32, vp, vp]
     lib.orc_paths.restype = i64
     lib.orc_paths.argtypes = [i64, vp, vp, vp, i64]
     lib.orc_triangles.restype = i64
@@ -105,18 +105,32 @@ def to_int(limbs):
 
 
 def count(row_ptr, col, *, kmax: int = -1, vertex: bool = False, edge: bool = False,
-          roots=None, threads: int = 1, nl: int | None = None, hist_dim: int = 0):
+          roots=None, threads: int = 1, nl: int | None = None, hist_dim: int = 0, dag=None):
     """Exact clique counts, k = 0..kmax (kmax < 0: every k up to alpha+1).
 
     Returns a dict: ``C`` (list of ints), ``cv`` / ``ce`` (limb arrays
     [n][K][nl] / [m][K][nl], only if asked), ``nl``, ``alpha``, ``kmax`` and
-    SCT statistics ``nodes``, ``leaves``, ``sum_s``; ``hist`` ((h, p) leaf
-    histogram) if ``hist_dim`` > 0.
+    SCT statistics ``nodes``, ``leaves``, ``sum_s`` and ``chain`` (the nodes
+    below the topmost clique label of each path, which a walk that closes
+    clique labels at once never visits); ``hist`` ((h, p) leaf histogram) if
+    ``hist_dim`` > 0.  ``dag = (orow, ocol)`` walks that acyclic orientation
+    (out-lists sorted ascending) instead of the degeneracy order; ``alpha``
+    is then its largest out-degree.
     """
     row_ptr, col = _csr(row_ptr, col)
     n = len(row_ptr) - 1
     m = int(row_ptr[-1]) // 2
-    _, _, alpha = orient(row_ptr, col)
+    if dag is not None:
+        orow = np.ascontiguousarray(dag[0], dtype=np.int64)
+        ocol = np.ascontiguousarray(dag[1], dtype=np.uint32)
+        if len(orow) != n + 1:
+            raise ValueError("dag row pointers need n + 1 entries")
+        alpha = int(np.diff(orow).max()) if n else 0
+        ocol_buf = ocol if len(ocol) else np.zeros(1, dtype=np.uint32)
+        dag_ptrs = (orow.ctypes.data, ocol_buf.ctypes.data)
+    else:
+        _, _, alpha = orient(row_ptr, col)
+        dag_ptrs = (None, None)
     if kmax < 0:
         kmax = alpha + 1
     if nl is None:
@@ -137,11 +151,11 @@ def count(row_ptr, col, *, kmax: int = -1, vertex: bool = False, edge: bool = Fa
     rc = _load().orc_count(n, row_ptr.ctypes.data, col.ctypes.data, kmax, nl, C.ctypes.data,
                            cv.ctypes.data if vertex else None, ce.ctypes.data if edge else None,
                            rptr, nroots, threads, stats.ctypes.data,
-                           hist.ctypes.data if hist_dim else None, hist_dim)
+                           hist.ctypes.data if hist_dim else None, hist_dim, *dag_ptrs)
     if rc:
         raise RuntimeError(f"oracle: {ERRORS.get(rc, rc)}")
     out = dict(C=to_int(C), nl=nl, alpha=alpha, kmax=kmax,
-               nodes=int(stats[0]), leaves=int(stats[1]), sum_s=int(stats[2]))
+               nodes=int(stats[0]), leaves=int(stats[1]), sum_s=int(stats[2]), chain=int(stats[5]))
     if vertex:
         out["cv"] = cv[:n]
     if edge:

@@ -195,6 +195,80 @@ static int graph_init(graph *g, int64_t n, const int64_t *rp, const uint32_t *co
     return ORC_OK;
 }
 
+/* The same graph with a caller's acyclic orientation instead of the
+ * degeneracy order (any acyclic orientation counts every clique once, at its
+ * first vertex): out-lists orow/ocol, each sorted ascending.  They must be an
+ * orientation of the graph -- every edge in exactly one of its endpoints'
+ * lists, nothing else -- and acyclic (Kahn's topological sort consumes every
+ * vertex); else ORC_EINVAL.  rank[] becomes the topological position. */
+static int graph_init_dag(graph *g, int64_t n, const int64_t *rp, const uint32_t *col, const int64_t *orow,
+                          const uint32_t *ocol)
+{
+    memset(g, 0, sizeof(*g));
+    g->n = n;
+    g->rp = rp;
+    g->col = col;
+    g->m = rp[n] / 2;
+    g->up = (int64_t *)malloc(((size_t)n + 1) * sizeof(int64_t));
+    g->rank = (uint32_t *)malloc(((size_t)n + 1) * sizeof(uint32_t));
+    g->orp = (int64_t *)malloc(((size_t)n + 1) * sizeof(int64_t));
+    g->ocol = (uint32_t *)malloc(((size_t)g->m + 1) * sizeof(uint32_t));
+    int64_t *indeg = (int64_t *)calloc((size_t)n + 1, sizeof(int64_t));
+    uint32_t *queue = (uint32_t *)malloc(((size_t)n + 1) * sizeof(uint32_t));
+    int rc = ORC_OK;
+    if (!g->up || !g->rank || !g->orp || !g->ocol || !indeg || !queue) rc = ORC_ENOMEM;
+    if (!rc && (orow[0] != 0 || orow[n] != g->m)) rc = ORC_EINVAL;
+    for (int64_t v = 0; !rc && v < n; ++v) {
+        if (orow[v + 1] < orow[v]) { rc = ORC_EINVAL; break; }
+        for (int64_t i = orow[v]; i < orow[v + 1]; ++i) {
+            const uint32_t u = ocol[i];
+            if ((uint64_t)u >= (uint64_t)n || (i > orow[v] && ocol[i - 1] >= u) || !row_find(g, (uint32_t)v, u, NULL)) {
+                rc = ORC_EINVAL;
+                break;
+            }
+            indeg[u]++;
+        }
+    }
+    /* every edge in exactly one list: lists hold m entries in all, each a
+     * neighbour, and no edge is in both of its endpoints' lists */
+    for (int64_t v = 0; !rc && v < n; ++v)
+        for (int64_t i = orow[v]; i < orow[v + 1] && !rc; ++i) {
+            const uint32_t u = ocol[i];
+            int64_t lo = orow[u], hi = orow[u + 1];
+            while (lo < hi) {
+                int64_t mid = lo + (hi - lo) / 2;
+                if (ocol[mid] < (uint32_t)v) lo = mid + 1; else hi = mid;
+            }
+            if (lo < orow[u + 1] && ocol[lo] == (uint32_t)v) rc = ORC_EINVAL;
+        }
+    if (!rc) {
+        int64_t head = 0, tail = 0;
+        for (int64_t v = 0; v < n; ++v) if (!indeg[v]) queue[tail++] = (uint32_t)v;
+        while (head < tail) {
+            const uint32_t v = queue[head];
+            g->rank[v] = (uint32_t)head++;
+            for (int64_t i = orow[v]; i < orow[v + 1]; ++i)
+                if (--indeg[ocol[i]] == 0) queue[tail++] = ocol[i];
+        }
+        if (tail != n) rc = ORC_EINVAL; /* a cycle */
+    }
+    if (!rc) {
+        g->up[0] = 0;
+        for (int64_t u = 0; u < n; ++u) {
+            int64_t c = 0;
+            for (int64_t e = rp[u]; e < rp[u + 1]; ++e) c += col[e] > u;
+            g->up[u + 1] = g->up[u] + c;
+        }
+        for (int64_t v = 0; v <= n; ++v) g->orp[v] = orow[v];
+        for (int64_t i = 0; i < g->m; ++i) g->ocol[i] = ocol[i];
+        for (int64_t v = 0; v < n; ++v)
+            if (orow[v + 1] - orow[v] > g->alpha) g->alpha = (int)(orow[v + 1] - orow[v]);
+    }
+    free(indeg);
+    free(queue);
+    return rc;
+}
+
 static void graph_free(graph *g)
 {
     free(g->up); free(g->rank); free(g->orp); free(g->ocol);
@@ -213,6 +287,8 @@ typedef struct {
     size_t top, cap;
     int ovf, err;
     uint64_t nodes, leaves, sum_s;
+    uint64_t chain;          /* nodes below the topmost clique labels (see visit) */
+    int clq;                 /* the parent node's label is a clique */
     uint64_t *hist;          /* optional leaf histogram over (h, p) */
     int hdim;
     int32_t *paths;          /* optional leaf dump: h, p, H..., P... */
@@ -297,6 +373,14 @@ static void visit(walker *w, const uint32_t *v, const uint8_t *A, int s)
         if (deg[i] > deg[pi]) pi = i;
     }
 
+    /* A nonempty label that is a clique has one continuation: each pivot is
+     * adjacent to the rest, so its subtree is the chain of pivot children
+     * S, S minus one member, ..., {} -- |S| nodes below S.  Count them at the
+     * topmost such label of a path (statistics only). */
+    int is_clique = 1;
+    for (int i = 0; i < s; ++i) if (deg[i] != s - 1) { is_clique = 0; break; }
+    if (is_clique && !w->clq) w->chain += (uint64_t)s;
+
     /* pivot child: N(S,p), link (p, pivot) */
     int cs = 0;
     for (int j = 0; j < s; ++j) if (A[(size_t)pi * s + j]) idx[cs++] = j;
@@ -305,7 +389,10 @@ static void visit(walker *w, const uint32_t *v, const uint8_t *A, int s)
         for (int b = 0; b < cs; ++b) cA[(size_t)a * cs + b] = A[(size_t)idx[a] * s + idx[b]];
     }
     w->P[w->p++] = v[pi];
+    const int parent_clq = w->clq;
+    w->clq = is_clique;
     visit(w, cv, cA, cs);
+    w->clq = parent_clq;
     w->p--;
 
     /* non-neighbours of p in S \ {p}, ascending: v_1 < ... < v_l */
@@ -327,7 +414,10 @@ static void visit(walker *w, const uint32_t *v, const uint8_t *A, int s)
             for (int b = 0; b < cs; ++b) cA[(size_t)a * cs + b] = A[(size_t)idx[a] * s + idx[b]];
         }
         w->H[w->h++] = v[vi];
+        const int parent_clq = w->clq;
+        w->clq = 0; /* a label with a hold child is not a clique */
         visit(w, cv, cA, cs);
+        w->clq = parent_clq;
         w->h--;
     }
     w->top = mark;
@@ -347,6 +437,7 @@ static void visit_root(walker *w, uint32_t r)
             A[(size_t)i * s + j] = (uint8_t)(i != j && is_adj(g, v[i], v[j]));
     w->h = 0;
     w->p = 0;
+    w->clq = 0;
     w->H[w->h++] = r;
     visit(w, v, A, s);
     w->top = mark;
@@ -424,17 +515,20 @@ int orc_orient(int64_t n, const int64_t *rp, const uint32_t *col, uint32_t *rank
  * Output arrays must be zeroed by the caller.  roots/nroots restrict the walk
  * to the given root vertices (NULL: all).  nthreads > 1 is allowed only for
  * global counts (private arrays per thread, summed at the end).
- * stats[0..4] = nodes (excluding the tree's root), leaves, sum of |S| over
- * internal nodes, alpha, kmax used.  hist (hdim x hdim) counts leaves by
+ * stats[0..5] = nodes (excluding the tree's root), leaves, sum of |S| over
+ * internal nodes, alpha, kmax used, and the nodes below the topmost clique
+ * labels of the paths (the pivot chains that a walk closing clique labels
+ * at once skips).  orow_in/ocol_in (NULL: the degeneracy order) give an
+ * acyclic orientation to walk instead (see graph_init_dag).  hist (hdim x hdim) counts leaves by
  * (h, p).  Returns 0, or an ORC_* error (ORC_EOVERFLOW if nl is too small).
  */
 int orc_count(int64_t n, const int64_t *rp, const uint32_t *col, int kmax, int nl, uint32_t *C,
               uint32_t *cv, uint32_t *ce, const uint32_t *roots, int64_t nroots, int nthreads,
-              uint64_t *stats, uint64_t *hist, int hdim)
+              uint64_t *stats, uint64_t *hist, int hdim, const int64_t *orow_in, const uint32_t *ocol_in)
 {
     if (n < 0 || nl < 1 || (nthreads > 1 && (cv || ce))) return ORC_EINVAL;
     graph g;
-    int rc = graph_init(&g, n, rp, col);
+    int rc = orow_in ? graph_init_dag(&g, n, rp, col, orow_in, ocol_in) : graph_init(&g, n, rp, col);
     if (rc) { graph_free(&g); return rc; }
     if (kmax < 0) kmax = g.alpha + 1;
     if (!roots) nroots = n;
@@ -470,7 +564,7 @@ int orc_count(int64_t n, const int64_t *rp, const uint32_t *col, int kmax, int n
             for (int t = 0; t < nthreads; ++t) pthread_join(th[t], NULL);
         }
     }
-    uint64_t st[3] = {0, 0, 0};
+    uint64_t st[4] = {0, 0, 0, 0};
     for (int t = 0; t < nthreads; ++t) {
         walker *w = &wk[t].w;
         if (!rc && w->err) rc = w->err;
@@ -480,6 +574,7 @@ int orc_count(int64_t n, const int64_t *rp, const uint32_t *col, int kmax, int n
         st[0] += w->nodes;
         st[1] += w->leaves;
         st[2] += w->sum_s;
+        st[3] += w->chain;
         if (hist && w->hist)
             for (size_t i = 0; i < (size_t)hdim * hdim; ++i) hist[i] += w->hist[i];
         free(w->C);
@@ -492,6 +587,7 @@ int orc_count(int64_t n, const int64_t *rp, const uint32_t *col, int kmax, int n
         stats[2] = st[2];
         stats[3] = (uint64_t)g.alpha;
         stats[4] = (uint64_t)kmax;
+        stats[5] = st[3];
     }
     free(wk);
     free(th);

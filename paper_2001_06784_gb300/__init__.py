@@ -65,6 +65,22 @@ class Dag:
                                             _stream_handle(stream, self.device)))
         return out
 
+    def out_lists(self, stream=None):
+        """The orientation: (orow int64 [n+1], ocol int32 [m]) device tensors,
+        N+(v) = ocol[orow[v]:orow[v+1]] sorted by id (pvt_dag_out_lists)."""
+        orow = torch.empty(self.n + 1, dtype=torch.int64, device=self.device)
+        ocol = torch.empty(max(self.m, 1), dtype=torch.int32, device=self.device)
+        _lib.check(_lib.lib().pvt_dag_out_lists(self._h, ctypes.c_void_p(orow.data_ptr()),
+                                                ctypes.c_void_p(ocol.data_ptr()), _stream_handle(stream, self.device)))
+        return orow, ocol[:self.m]
+
+    def leaf_depths(self, stream=None):
+        """Leaves of the last global count by depth h + p, numpy uint64
+        [alpha+2] (pvt_dag_leaf_depths)."""
+        out = np.zeros(self.alpha + 2, dtype=np.uint64)
+        _lib.check(_lib.lib().pvt_dag_leaf_depths(self._h, out.ctypes.data, _stream_handle(stream, self.device)))
+        return out
+
     def count_global(self, kmax=None, W=None, out=None, stream=None):
         """C_k for k = 0..kmax as an int64 tensor [kmax+1, W] of 64-bit words
         (little-endian, reinterpret as unsigned)."""
@@ -134,21 +150,23 @@ class Dag:
         pol = _lib.Policy()
         _lib.check(_lib.lib().pvt_dag_get_policy(self._h, ctypes.byref(pol)))
         return dict(persistent=bool(pol.persistent), chunk=pol.chunk, split=list(pol.split), graph=bool(pol.graph),
-                    frames=bool(pol.frames))
+                    frames=bool(pol.frames), wait_limit_us=pol.wait_limit_us)
 
     def set_policy(self, persistent: bool = True, chunk: int = 4, split=None, graph: bool = False,
-                   frames: bool = True):
+                   frames: bool = True, wait_limit_us: int = 0):
         """Launch policy of the walk kernels: persistent warps with a device
         work queue (default) or the plain one-warp-per-root form; per
         out-degree class whether heavy roots split across warps (7 flags,
         default: every class above out-degree 32); whether global counts
         replay a recorded CUDA graph; whether global counts walk the small
-        labels of the classes above 32 in a second, lighter kernel."""
+        labels of the classes above 32 in a second, lighter kernel;
+        wait_limit_us > 0 shortens the bounded device waits (a test of the
+        PVT_ETIMEOUT path)."""
         split = [0, 0, 1, 1, 1, 1, 1] if split is None else [int(x) for x in split]
         if len(split) != 7:
             raise ValueError("split needs one flag per out-degree class (7)")
         pol = _lib.Policy(1 if persistent else 0, int(chunk), (ctypes.c_int32 * 7)(*split), 1 if graph else 0,
-                          1 if frames else 0)
+                          1 if frames else 0, int(wait_limit_us))
         _lib.check(_lib.lib().pvt_dag_set_policy(self._h, ctypes.byref(pol)))
 
     def autotune(self, kmax=None, W=None, out=None, stream=None):
@@ -163,7 +181,7 @@ class Dag:
                                                _stream_handle(stream, self.device), ctypes.byref(pol),
                                                ms.ctypes.data))
         return (dict(persistent=bool(pol.persistent), chunk=pol.chunk, split=list(pol.split),
-                     graph=bool(pol.graph), frames=bool(pol.frames)), ms, out)
+                     graph=bool(pol.graph), frames=bool(pol.frames), wait_limit_us=pol.wait_limit_us), ms, out)
 
     def set_profiling(self, on: bool):
         _lib.check(_lib.lib().pvt_dag_set_profiling(self._h, 1 if on else 0))

@@ -30,7 +30,7 @@ class Stats(ctypes.Structure):
 class Policy(ctypes.Structure):
     """pvt_policy (include/pivoter.h)."""
     _fields_ = [("persistent", ctypes.c_int32), ("chunk", ctypes.c_int32), ("split", ctypes.c_int32 * 7),
-                ("graph", ctypes.c_int32), ("frames", ctypes.c_int32)]
+                ("graph", ctypes.c_int32), ("frames", ctypes.c_int32), ("wait_limit_us", ctypes.c_int32)]
 
 
 class ServerConfig(ctypes.Structure):
@@ -47,7 +47,7 @@ EXPORTS = ("pvt_orient", "pvt_dag_info", "pvt_dag_cores", "pvt_local_distributio
            "pvt_dag_get_policy", "pvt_dag_autotune",
            "pvt_count_global_noalloc", "pvt_server_create", "pvt_server_submit", "pvt_server_wait",
            "pvt_server_result", "pvt_server_destroy", "pvt_dag_free",
-           "pvt_last_error", "pvt_measure_popc_rate")
+           "pvt_last_error", "pvt_measure_popc_rate", "pvt_dag_leaf_depths", "pvt_dag_out_lists")
 
 
 class PivoterError(RuntimeError):
@@ -76,6 +76,10 @@ def load(path: str = LIB_PATH):
     lib.pvt_local_distribution.argtypes = [vp, i64, i32, i32, i32, vp, vp, ctypes.POINTER(i64), vp]
     lib.pvt_dag_cores.restype = i32
     lib.pvt_dag_cores.argtypes = [vp, vp, vp]
+    lib.pvt_dag_leaf_depths.restype = i32
+    lib.pvt_dag_leaf_depths.argtypes = [vp, vp, vp]
+    lib.pvt_dag_out_lists.restype = i32
+    lib.pvt_dag_out_lists.argtypes = [vp, vp, vp, vp]
     for fn in ("pvt_count_global", "pvt_count_local_vertex", "pvt_count_local_edge"):
         f = getattr(lib, fn)
         f.restype = i32

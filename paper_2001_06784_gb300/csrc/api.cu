@@ -299,6 +299,25 @@ pvt_status pvt_dag_cores(const pvt_dag *dag, uint32_t *core, void *stream)
     return PVT_OK;
 }
 
+pvt_status pvt_dag_out_lists(const pvt_dag *dag, int64_t *orow, uint32_t *ocol, void *stream)
+{
+    if (!dag || !orow || (!ocol && dag->m > 0)) {
+        set_error("pvt_dag_out_lists: invalid argument");
+        return PVT_EINVAL;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    PVT_CK(cudaMemcpyAsync(orow, dag->orow, (size_t)(dag->n + 1) * sizeof(int64_t), cudaMemcpyDeviceToDevice, s));
+    if (dag->m > 0)
+        PVT_CK(cudaMemcpyAsync(ocol, dag->ocol, (size_t)dag->m * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s));
+    PVT_CK(cudaStreamSynchronize(s));
+    return PVT_OK;
+}
+
+pvt_status pvt_dag_leaf_depths(pvt_dag *dag, uint64_t *depth, void *stream)
+{
+    return leaf_depths(dag, depth, (cudaStream_t)stream);
+}
+
 pvt_status pvt_count_global(pvt_dag *dag, int32_t kmax, int32_t W, uint64_t *C, void *stream)
 {
     const HostRange range("pvt_count_global");
@@ -362,7 +381,8 @@ pvt_status pvt_dag_set_policy(pvt_dag *dag, const pvt_policy *policy)
 {
     bool ok = dag && policy && (policy->persistent == 0 || policy->persistent == 1) && policy->chunk >= 1 &&
               policy->chunk <= 32 && (policy->graph == 0 || policy->graph == 1) &&
-              (policy->frames == 0 || policy->frames == 1);
+              (policy->frames == 0 || policy->frames == 1) && policy->wait_limit_us >= 0 &&
+              policy->wait_limit_us <= 1000000000;
     for (int c = 0; ok && c < NCLASS; ++c) ok = policy->split[c] == 0 || policy->split[c] == 1;
     if (!ok) {
         set_error("pvt_dag_set_policy: invalid argument");

@@ -44,6 +44,12 @@ extern template pvt_status launch_batch_class<16, MODE_GLOBAL>(const BatchGraph 
 extern template pvt_status launch_batch_class<16, MODE_VERTEX>(const BatchGraph *, const uint64_t *, unsigned, unsigned *, const unsigned long long *, int, unsigned *, unsigned long long *, int, cudaStream_t);
 extern template pvt_status launch_batch_class<16, MODE_EDGE>(const BatchGraph *, const uint64_t *, unsigned, unsigned *, const unsigned long long *, int, unsigned *, unsigned long long *, int, cudaStream_t);
 
+// The test-settable limit of the bounded device waits (policy.wait_limit_us).
+static void apply_wait_limit(const pvt_dag *g, CountArgs &A)
+{
+    if (g->policy.wait_limit_us > 0) A.idle_ns = A.slot_ns = 1000ull * (unsigned long long)g->policy.wait_limit_us;
+}
+
 // ------------------------------------------------------ small kernels
 
 // Roots with no out-neighbour: one path each with h = 1, p = 0.
@@ -300,13 +306,16 @@ static void begin_call(pvt_dag *g)
 }
 
 // Copy the walk statistics back, synchronise and check the device status.
-static pvt_status end_call(pvt_dag *g, cudaStream_t s, const char *fn)
+// Roots with no out-neighbour are one node and one leaf each (h = 1, p = 0)
+// when kmax >= 1; they are tallied without a walk, and counted here.
+static pvt_status end_call(pvt_dag *g, cudaStream_t s, const char *fn, int32_t kmax)
 {
     PVT_CK(cudaMemcpyAsync(g->h_stats, g->d_stats, (3 + NCLASS + 2) * sizeof(unsigned long long),
                            cudaMemcpyDeviceToHost, s));
     pvt_status st = check_device(g, s, fn);
-    g->stats.sct_nodes = g->h_stats[0];
-    g->stats.sct_leaves = g->h_stats[1];
+    const uint64_t trivial = kmax >= 1 ? (uint64_t)g->wcnt[0] : 0;
+    g->stats.sct_nodes = g->h_stats[0] + trivial;
+    g->stats.sct_leaves = g->h_stats[1] + trivial;
     g->stats.pivot_words = g->h_stats[2];
     for (int c = 0; c < NCLASS; ++c) g->stats.class_words[c] = g->h_stats[3 + c];
     g->stats.frame_words = g->h_stats[3 + FRAMES_SLOT];
@@ -361,6 +370,7 @@ static pvt_status enqueue_global(pvt_dag *g, int32_t kmax, int32_t W, uint64_t *
     A.kmax = kmax;
     A.err = g->d_err;
     A.stats = g->d_stats;
+    apply_wait_limit(g, A);
     if ((st = launch_all<MODE_GLOBAL>(g, A, s)) != PVT_OK) return st;
     phase_begin(g, PH_FINISH, s);
     if (kmax >= 1) {
@@ -433,14 +443,55 @@ pvt_status count_global(pvt_dag *g, int32_t kmax, int32_t W, uint64_t *C, cudaSt
     if (st != PVT_OK) return st;
     begin_call(g);
     const bool use_graph = g->policy.graph != 0 && !g->serial;
+    g->hist_valid = false;
     if (use_graph && g->graph_exec && g->graph_kmax == kmax && g->graph_W == W && g->graph_out == C) {
         PVT_CK(cudaGraphLaunch(g->graph_exec, s));
         g->stats.launches = g->graph_launches;
-        return end_call(g, s, "pvt_count_global");
+        st = end_call(g, s, "pvt_count_global", kmax);
+        g->hist_valid = st == PVT_OK;
+        return st;
     }
     if ((st = enqueue_global(g, kmax, W, C, s)) != PVT_OK) return st;
-    if ((st = end_call(g, s, "pvt_count_global")) != PVT_OK) return st;
+    if ((st = end_call(g, s, "pvt_count_global", kmax)) != PVT_OK) return st;
+    g->hist_valid = true;
     return use_graph ? record_graph(g, kmax, W, C) : PVT_OK;
+}
+
+// Leaves by depth d = h + p (links on the root-to-leaf path) from the (h, p)
+// histogram: out[d] = sum over h of hist[h][d - h], d = 0..H-1.  A leaf
+// deeper than H-1 (impossible: a path's links form a clique of at most
+// alpha + 1 vertices) is a range error.
+__global__ void __launch_bounds__(256) k_leaf_depths(const unsigned long long *__restrict__ hist, int H,
+                                                     unsigned long long *out, unsigned *err)
+{
+    for (int d = threadIdx.x; d <= 2 * (H - 1); d += blockDim.x) {
+        unsigned long long a = 0;
+        for (int h = max(0, d - (H - 1)); h <= min(d, H - 1); ++h) a += hist[(size_t)h * H + (d - h)];
+        if (d < H) out[d] = a;
+        else if (a) atomicOr(err, DERR_RANGE);
+    }
+}
+
+pvt_status leaf_depths(pvt_dag *g, uint64_t *depth, cudaStream_t s)
+{
+    if (!g || !depth) {
+        set_error("pvt_dag_leaf_depths: invalid argument");
+        return PVT_EINVAL;
+    }
+    if (!g->hist_valid) {
+        set_error("pvt_dag_leaf_depths: no completed pvt_count_global on this dag");
+        return PVT_EINVAL;
+    }
+    const int H = g->alpha + 2;
+    unsigned long long *d_out = nullptr;
+    PVT_CK(cudaMallocAsync(&d_out, (size_t)H * sizeof(unsigned long long), s));
+    PVT_CK(cudaMemsetAsync(g->d_err, 0, sizeof(unsigned), s));
+    k_leaf_depths<<<1, 256, 0, s>>>(g->hist.p, H, d_out, g->d_err);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(depth, d_out, (size_t)H * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s);
+    cudaFreeAsync(d_out, s);
+    if (e != cudaSuccess) return cuda_fail(e, "pvt_dag_leaf_depths");
+    return check_device(g, s, "pvt_dag_leaf_depths");
 }
 
 // ------------------------------------------- root ranges and checkpoints
@@ -541,6 +592,7 @@ pvt_status count_hist(pvt_dag *g, int64_t begin, int64_t end, int32_t kmax, uint
     A.kmax = kmax;
     A.err = g->d_err;
     A.stats = g->d_stats;
+    apply_wait_limit(g, A);
     if ((st = launch_all<MODE_GLOBAL>(g, A, s)) != PVT_OK) return st;
     if (kmax >= 1) {
         int64_t walked = 0;
@@ -550,7 +602,7 @@ pvt_status count_hist(pvt_dag *g, int64_t begin, int64_t end, int32_t kmax, uint
         PVT_CK(cudaGetLastError());
         g->stats.launches++;
     }
-    return end_call(g, s, "pvt_count_hist");
+    return end_call(g, s, "pvt_count_hist", kmax);
 }
 
 pvt_status combine_hist(pvt_dag *g, const uint64_t *hist, int32_t kmax, int32_t W, uint64_t *C, cudaStream_t s)
@@ -569,7 +621,7 @@ pvt_status combine_hist(pvt_dag *g, const uint64_t *hist, int32_t kmax, int32_t 
                                        W, kmax, reinterpret_cast<unsigned long long *>(C), g->d_err);
     PVT_CK(cudaGetLastError());
     g->stats.launches++;
-    return end_call(g, s, "pvt_combine_hist");
+    return end_call(g, s, "pvt_combine_hist", -1);
 }
 
 // Per-class minimum over three candidate policies, classes timed one at a time.
@@ -581,9 +633,9 @@ pvt_status autotune(pvt_dag *g, int32_t kmax, int32_t W, uint64_t *C, cudaStream
         return PVT_EINVAL;
     }
     static const pvt_policy cand[3] = {
-        {1, 4, {0, 0, 1, 1, 1, 1, 1}, 0, 1},
-        {1, 1, {0, 0, 0, 0, 0, 0, 0}, 0, 1},
-        {1, 16, {0, 0, 1, 1, 1, 1, 1}, 0, 1},
+        {1, 4, {0, 0, 1, 1, 1, 1, 1}, 0, 1, 0},
+        {1, 1, {0, 0, 0, 0, 0, 0, 0}, 0, 1, 0},
+        {1, 16, {0, 0, 1, 1, 1, 1, 1}, 0, 1, 0},
     };
     const pvt_policy saved = g->policy;
     const bool saved_prof = g->profiling;
@@ -595,6 +647,7 @@ pvt_status autotune(pvt_dag *g, int32_t kmax, int32_t W, uint64_t *C, cudaStream
     for (int pass = 0; pass < 2 && st == PVT_OK; ++pass)
         for (int c = 0; c < 3 && st == PVT_OK; ++c) {
             g->policy = cand[c];
+            g->policy.wait_limit_us = saved.wait_limit_us;
             st = count_global(g, kmax, W, C, s);
             for (int cls = 1; st == PVT_OK && cls < NCLASS; ++cls) {
                 float x = 0.f;
@@ -658,9 +711,10 @@ pvt_status count_local(pvt_dag *g, int32_t kmax, int32_t W, uint64_t *out, bool 
     A.kmax = kmax;
     A.err = g->d_err;
     A.stats = g->d_stats;
+    apply_wait_limit(g, A);
     st = edge ? launch_all<MODE_EDGE>(g, A, s) : launch_all<MODE_VERTEX>(g, A, s);
     if (st != PVT_OK) return st;
-    return end_call(g, s, fn);
+    return end_call(g, s, fn, kmax);
 }
 
 
@@ -878,7 +932,7 @@ extern "C" pvt_status pvt_count_global_noalloc(int64_t n, const int64_t *orow, c
 {
     const pvt::HostRange range("pvt_count_global_noalloc");
     using namespace pvt;
-    if (n < 0 || n > 0xFFFFFFFEll || (n > 0 && !orow) || !C || kmax < 0 || alpha < 0 || W < 1) {
+    if (n < 0 || n > 0xFFFFFFFEll || (n > 0 && (!orow || !ocol)) || !C || kmax < 0 || alpha < 0 || W < 1) {
         set_error("pvt_count_global_noalloc: invalid argument");
         return PVT_EINVAL;
     }

@@ -81,7 +81,7 @@ struct pvt_dag {
     unsigned long long *h_stats = nullptr;  // pinned host copy
     pvt_stats stats = {};
     bool profiling = false;
-    pvt_policy policy = {1, 4, {0, 0, 1, 1, 1, 1, 1}, 0, 1};
+    pvt_policy policy = {1, 4, {0, 0, 1, 1, 1, 1, 1}, 0, 1, 0};
     pvt::DevBuf<uint32_t> cframes;  // compacted frames emitted by the wide walks
     bool serial = false;           // launch the classes one after another on the caller's stream
     bool capturing = false;        // recording a CUDA graph: no phase events
@@ -92,6 +92,7 @@ struct pvt_dag {
     cudaEvent_t ev_t0[pvt::NPHASE] = {}, ev_t1[pvt::NPHASE] = {};
     bool phase_used[pvt::NPHASE] = {};
     pvt::DevBuf<uint32_t> gstack[pvt::NCLASS];  // DFS stacks of the wide classes (global memory)
+    bool hist_valid = false;       // hist holds the leaves of the last completed global count
 };
 
 namespace pvt {
@@ -162,6 +163,7 @@ pvt_status autotune(pvt_dag *g, int32_t kmax, int32_t W, uint64_t *C, cudaStream
                     float *ms);
 pvt_status count_hist(pvt_dag *g, int64_t begin, int64_t end, int32_t kmax, uint64_t *hist, cudaStream_t s);
 pvt_status combine_hist(pvt_dag *g, const uint64_t *hist, int32_t kmax, int32_t W, uint64_t *C, cudaStream_t s);
+pvt_status leaf_depths(pvt_dag *g, uint64_t *depth, cudaStream_t s);
 void drop_graph(pvt_dag *g);
 
 // Exclusive prefix sum of uint32 counts into int64 offsets (out has n+1 entries).

@@ -114,6 +114,9 @@ __device__ __forceinline__ const unsigned long long *binom_at(const unsigned lon
 
 // ------------------------------------------------------- leaf tallies
 
+constexpr unsigned long long SPLIT_IDLE_LIMIT_NS = 120000000000ull;  // 120 s without progress (profilers slow items a lot)
+constexpr unsigned long long SPLIT_SLOT_LIMIT_NS = 2000000000ull;  // 2 s for a ring slot to free up
+
 struct CountArgs {
     const int64_t *orow;
     const uint32_t *ocol;
@@ -146,6 +149,9 @@ struct CountArgs {
     unsigned long long *emit_count;  // compacted subtrees met so far (passes emit_cap once the
                                      // buffer is full; 64-bit: long walks meet billions)
     unsigned emit_cap;
+    // bounded waits: an idle warp gives up after idle_ns without progress, a
+    // donor after slot_ns for a ring slot (policy.wait_limit_us overrides both)
+    unsigned long long idle_ns = SPLIT_IDLE_LIMIT_NS, slot_ns = SPLIT_SLOT_LIMIT_NS;
 };
 
 // Work queue of a split launch, a ring of qcap slots.  Idle warps take a
@@ -247,8 +253,6 @@ __device__ __forceinline__ void close_small(unsigned long long *shist, const Cou
 constexpr int DONATE_MIN_WIDE = 16;     // members of a wide frame's label
 constexpr int DONATE_MIN_COMPACT = 14;  // members of a compacted frame's label
 
-constexpr unsigned long long SPLIT_IDLE_LIMIT_NS = 120000000000ull;  // 120 s without progress (profilers slow items a lot)
-constexpr unsigned long long SPLIT_SLOT_LIMIT_NS = 2000000000ull;  // 2 s for a ring slot to free up
 
 __device__ __forceinline__ unsigned vload(const unsigned *p) { return *(const volatile unsigned *)p; }
 __device__ __forceinline__ unsigned long long vload64(const uint32_t *p)
@@ -260,10 +264,12 @@ __device__ __forceinline__ unsigned long long *qword(uint32_t *p)
     return reinterpret_cast<unsigned long long *>(p);
 }
 
-// Lane 0: are warps waiting on tickets that no frame fills yet?
+// Lane 0: are warps waiting on tickets that no frame fills yet?  (Not once
+// a wait has given up: the waiting warps have left, and a donation would
+// only wait for a slot that no one frees.)
 __device__ __forceinline__ bool queue_hungry(const CountArgs &A)
 {
-    return vload64(A.qctl + Q_HEAD) > vload64(A.qctl + Q_TAIL);
+    return vload64(A.qctl + Q_HEAD) > vload64(A.qctl + Q_TAIL) && !(vload(A.err) & DERR_TIMEOUT);
 }
 
 // Reserve the slot of the next frame (one more outstanding item); all lanes
@@ -280,7 +286,7 @@ __device__ __forceinline__ uint32_t *frame_reserve(const CountArgs &A, int lane,
             const unsigned want = (unsigned)(t64 - A.qcap + 1u), slot = t & (A.qcap - 1u);
             const unsigned long long t0 = global_ns();
             while (vload(A.qdone + slot) != want) {
-                if (global_ns() - t0 > SPLIT_SLOT_LIMIT_NS) { atomicOr(A.err, DERR_TIMEOUT); ok = 0; break; }
+                if (global_ns() - t0 > A.slot_ns) { atomicOr(A.err, DERR_TIMEOUT); ok = 0; break; }
                 __nanosleep(64);
             }
         }
@@ -977,7 +983,7 @@ __device__ __forceinline__ int queue_take(const CountArgs &A, unsigned nitems, u
         const unsigned out = vload(A.qctl + Q_OUT);
         if (out == 0 || (vload(A.err) & (DERR_STACK | DERR_RANGE | DERR_TIMEOUT))) { kind = 3; break; }
         if (out != last_out) { last_out = out; t0 = global_ns(); }
-        else if (global_ns() - t0 > SPLIT_IDLE_LIMIT_NS) { atomicOr(A.err, DERR_TIMEOUT); kind = 3; break; }
+        else if (global_ns() - t0 > A.idle_ns) { atomicOr(A.err, DERR_TIMEOUT); kind = 3; break; }
         __nanosleep(nap);
         nap = min(nap * 2u, 2048u);
     }

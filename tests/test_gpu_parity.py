@@ -115,6 +115,64 @@ def test_widest_class_global(pvt, make):
     assert ref["alpha"] > 512
 
 
+def limbs_as_words(limbs, W):
+    """Oracle limb array [..., nl] (32-bit, least significant first) as the
+    library's layout [..., W] of 64-bit words (higher limbs must be 0)."""
+    a = np.asarray(limbs, dtype=np.uint64)
+    if a.shape[-1] > 2 * W:
+        assert not a[..., 2 * W:].any(), "count wider than W words"
+        a = a[..., :2 * W]
+    pad = np.zeros(a.shape[:-1] + (2 * W,), dtype=np.uint64)
+    pad[..., :a.shape[-1]] = a
+    return pad[..., 0::2] | (pad[..., 1::2] << np.uint64(32))
+
+
+# Per-vertex and per-edge tables of roots in every wide out-degree class,
+# element by element against the oracle (Alg. 2 steps ht/pt and
+# hht/pht/ppt).  K_n without a few random edges keeps the tree small while
+# the roots' out-degrees sweep every class up to n - 2; (name, n, missing
+# edges, kmax of the vertex table, kmax of the edge table; -1 = every k).
+# Where the full per-edge table would not fit a test (m x (n+1) x W words),
+# the edge table is truncated at kmax (Sec. 4): entries k <= kmax are exact.
+LOCAL_CLASSES = [("65..128", 90, 12, -1, -1), ("129..256", 140, 10, -1, -1), ("257..512", 270, 6, -1, -1),
+                 ("257..512 branching", 300, 14, 6, 6), ("513..1024", 520, 8, -1, 6)]
+
+
+@pytest.fixture(scope="module")
+def local_refs():
+    """Oracle tables of every LOCAL_CLASSES case, computed on host threads
+    in parallel (the oracle's C code runs outside the interpreter lock)."""
+    import concurrent.futures as cf
+
+    def one(case):
+        _, n, miss, kv, ke = case
+        rp, col = graphs.clique_minus_random(n, miss, 1)
+        return (rp, col, oracle.count(rp, col, vertex=True, kmax=kv), oracle.count(rp, col, edge=True, kmax=ke))
+
+    with cf.ThreadPoolExecutor(max_workers=len(LOCAL_CLASSES)) as ex:
+        return dict(zip([c[0] for c in LOCAL_CLASSES], ex.map(one, LOCAL_CLASSES)))
+
+
+@pytest.mark.parametrize("case", LOCAL_CLASSES, ids=[c[0] for c in LOCAL_CLASSES])
+def test_local_tables_every_class(pvt, local_refs, case):
+    name, n = case[0], case[1]
+    rp, col, rv, re_ = local_refs[name]
+    dag = gpu_dag(pvt, rp, col)
+    assert dag.alpha == rv["alpha"] and dag.alpha >= n - 1 - case[2]
+    lo = {"65..128": 65, "129..256": 129, "257..512": 257, "257..512 branching": 257, "513..1024": 513}[name]
+    assert dag.alpha >= lo
+    W = dag.min_words
+    cv = dag.count_local_vertex(kmax=rv["kmax"]).cpu().numpy().view(np.uint64)
+    assert np.array_equal(cv, limbs_as_words(rv["cv"], W)), "per-vertex table differs from the oracle"
+    del cv
+    ce = dag.count_local_edge(kmax=re_["kmax"]).cpu().numpy().view(np.uint64)
+    assert np.array_equal(ce, limbs_as_words(re_["ce"], W)), "per-edge table differs from the oracle"
+    del ce
+    # the global counts of the same graph, as a cross-check of the tables' k range
+    assert pvt.to_ints(dag.count_global(kmax=rv["kmax"])) == rv["C"]
+    dag.free()
+
+
 @pytest.mark.parametrize("kmax", [0, 1, 2, 3, 5, 9])
 def test_truncation(pvt, kmax):
     rp, col = graphgen.generate(400, er_avg_deg=10.0, planted=[(2, 15, 25, 1.0)], seed=3)
@@ -370,4 +428,72 @@ def test_root_ranges_checkpoint(pvt, make):
     assert torch.equal(dag.count_hist(0, n, kmax=K), hist)
     with pytest.raises(pvt.PivoterError):
         dag.count_hist(3, 2, kmax=K)
+    dag.free()
+
+
+# ------------------------------------------------ SCT statistics, leaf depths
+
+@pytest.mark.parametrize("make", [lambda: graphs.complete(40), lambda: graphgen.workload("er2k_d20_clique30"),
+                                  lambda: graphs.clique_minus_random(300, 14, 7),
+                                  lambda: graphgen.generate(3000, er_avg_deg=12.0, planted=[(6, 20, 70, 0.9)], seed=13)])
+def test_sct_statistics_match_oracle(pvt, make):
+    """The tree the device walks is the oracle's SCT (Alg. 1) under the
+    device's own orientation: the same (h, p) leaf histogram, the same leaves,
+    leaf depths h + p, and nodes = the oracle's nodes minus the pivot chains
+    below clique labels (the device closes a clique label as one leaf).  The
+    oracle walks the out-lists the device exports, so both sides walk the
+    same roots' children."""
+    rp, col = make()
+    dag = gpu_dag(pvt, rp, col)
+    orow, ocol = dag.out_lists()
+    orow_h, ocol_h = orow.cpu().numpy(), ocol.cpu().numpy().view(np.uint32)
+    assert orow_h[-1] == dag.m and int(np.diff(orow_h).max()) == dag.alpha
+    H = dag.alpha + 2
+    ref = oracle.count(rp, col, dag=(orow_h, ocol_h), hist_dim=H)
+    assert ref["alpha"] == dag.alpha
+    assert pvt.to_ints(dag.count_global(kmax=ref["kmax"])) == ref["C"]
+    st = dag.stats()
+    assert st["sct_leaves"] == ref["leaves"]
+    assert st["sct_nodes"] == ref["nodes"] - ref["chain"]
+    depths = dag.leaf_depths()
+    want = np.zeros(H, dtype=np.uint64)
+    for h in range(H):
+        for p in range(H - h):
+            want[h + p] += ref["hist"][h, p]
+    assert np.array_equal(depths, want) and int(depths.sum()) == ref["leaves"]
+    hist = dag.count_hist(0, dag.n, kmax=ref["kmax"]).cpu().numpy().view(np.uint64)
+    assert np.array_equal(hist, ref["hist"])
+    dag.free()
+
+
+def test_leaf_depths_need_a_global_count(pvt):
+    rp, col = graphs.complete(6)
+    dag = gpu_dag(pvt, rp, col)
+    with pytest.raises(pvt.PivoterError) as ei:
+        dag.leaf_depths()
+    assert ei.value.status == 1
+    dag.count_global()
+    assert list(dag.leaf_depths()) == [0, 1, 1, 1, 1, 1, 1]  # root r: one leaf of depth 6 - r
+    dag.free()
+
+
+# ------------------------------------------------ failure detection
+
+def test_device_wait_expiry_returns_timeout(pvt):
+    """A bounded device-side wait that runs out ends the call with
+    PVT_ETIMEOUT and leaves the library usable.  K_258 puts one root in the
+    257..512 out-degree class, whose split launch has two warps: the second
+    waits for a donated frame while the first gathers 257 adjacency rows,
+    far longer than the 1 us limit set here, so the wait expires."""
+    rp, col = graphs.complete(258)
+    dag = gpu_dag(pvt, rp, col)
+    dag.set_policy(wait_limit_us=1)
+    assert dag.policy()["wait_limit_us"] == 1
+    with pytest.raises(pvt.PivoterError) as ei:
+        dag.count_global(kmax=8)
+    assert ei.value.status == 6 and "timed out" in str(ei.value)
+    dag.set_policy()
+    assert pvt.to_ints(dag.count_global(kmax=8)) == [0] + [math.comb(258, k) for k in range(1, 9)]
+    with pytest.raises(pvt.PivoterError):
+        dag.set_policy(wait_limit_us=-1)
     dag.free()

@@ -437,3 +437,76 @@ def test_root_parallel_ranges_add_up():
         assert r["C"][1] == len(roots)
         total = [a + b for a, b in zip(total, r["C"])]
     assert total == whole["C"]
+
+
+# ------------------------------------------ a caller's orientation; SCT statistics
+
+def id_orientation(row_ptr, col, reverse=False):
+    """Out-lists of the acyclic orientation "towards the larger id" (or the
+    smaller one), each sorted ascending."""
+    n = len(row_ptr) - 1
+    src = np.repeat(np.arange(n, dtype=np.int64), np.diff(row_ptr))
+    dst = col.astype(np.int64)
+    keep = dst < src if reverse else dst > src
+    orow = np.zeros(n + 1, dtype=np.int64)
+    orow[1:] = np.cumsum(np.bincount(src[keep], minlength=n))
+    return orow, dst[keep].astype(np.uint32)
+
+
+@pytest.mark.parametrize("make", [lambda: graphs.gnp(30, 0.4, 12), lambda: graphs.gnp(24, 0.6, 13),
+                                  lambda: graphs.multipartite([3, 2, 4, 1])])
+def test_any_acyclic_orientation_counts_the_same(make):
+    """Every clique is counted once at its first vertex under any acyclic
+    orientation (the paper's degeneracy order only bounds the cost, Lemma
+    degen): both id orientations give the brute-force tables."""
+    rp, col = make()
+    ref = oracle.count(rp, col)
+    C, cv, ce = brute_counts(rp, col, ref["kmax"])
+    for rev in (False, True):
+        r = oracle.count(rp, col, kmax=ref["kmax"], vertex=True, edge=True, dag=id_orientation(rp, col, rev))
+        assert r["C"] == C and oracle.to_int(r["cv"]) == cv and oracle.to_int(r["ce"]) == ce
+
+
+def test_bad_orientation_is_refused():
+    rp, col = graphs.gnp(12, 0.5, 3)
+    orow, ocol = id_orientation(rp, col)
+    # both directions of every edge
+    with pytest.raises(RuntimeError, match="invalid"):
+        oracle.count(rp, col, dag=(rp, col))
+    # the last edge of the last non-empty out-list dropped
+    last = int(np.nonzero(np.diff(orow))[0][-1])
+    bad_row, bad_col = orow.copy(), np.delete(ocol, orow[last + 1] - 1)
+    bad_row[last + 1:] -= 1
+    with pytest.raises(RuntimeError, match="invalid"):
+        oracle.count(rp, col, dag=(bad_row, bad_col))
+    # a directed cycle on a triangle 0 -> 1 -> 2 -> 0
+    trp, tcol = graphs.complete(3)
+    with pytest.raises(RuntimeError, match="invalid"):
+        oracle.count(trp, tcol, dag=(np.array([0, 1, 2, 3]), np.array([1, 2, 0], dtype=np.uint32)))
+
+
+@pytest.mark.parametrize("n", [1, 2, 5, 12, 40])
+def test_clique_chain_closed_forms(n):
+    """On K_n the label of root r (degeneracy order) is a clique of n-1-r
+    members, so the walk visits its chain of n-r nodes: nodes = n(n+1)/2, the
+    chains below the topmost clique labels hold C(n, 2) of them, and a walk
+    that closes clique labels at once visits n nodes, one per root."""
+    rp, col = graphs.complete(n)
+    r = oracle.count(rp, col)
+    assert r["nodes"] == n * (n + 1) // 2
+    assert r["chain"] == math.comb(n, 2)
+    assert r["leaves"] == n
+
+
+def test_clique_chain_disjoint_cliques_and_bounds():
+    """Disjoint cliques add up; on any graph the chains are at most the
+    nodes minus the leaves (every chain node but its end is internal)."""
+    sizes = [1, 4, 6, 9]
+    rp, col = graphs.disjoint_cliques(sizes)
+    r = oracle.count(rp, col)
+    assert r["chain"] == sum(math.comb(a, 2) for a in sizes)
+    assert r["nodes"] == sum(a * (a + 1) // 2 for a in sizes)
+    for make in (lambda: graphs.gnp(60, 0.3, 2), lambda: graphgen.workload("er2k_d20_clique30")):
+        rp, col = make()
+        r = oracle.count(rp, col)
+        assert 0 < r["chain"] and r["leaves"] <= r["nodes"] - r["chain"]
