@@ -287,6 +287,11 @@ pvt_status pvt_measure_popc_rate(double *pairs_per_s, void *stream);
  *               instead.  A wait that gives up ends the call with
  *               PVT_ETIMEOUT and leaves the library usable; the field
  *               exists to exercise that path (0 .. 10^9).
+ *   lanes       1 (default): in global counts of the persistent form, labels
+ *               of at most 32 members -- the roots of the <= 32 class and the
+ *               frames of the two-phase walk -- are walked one subtree per
+ *               lane, 32 subtrees per warp, instead of one per warp; 0: one
+ *               per warp.  The walked tree is the same either way.
  * Each field is checked: PVT_EINVAL for a value out of range.
  */
 typedef struct pvt_policy {
@@ -296,6 +301,7 @@ typedef struct pvt_policy {
     int32_t graph;
     int32_t frames;
     int32_t wait_limit_us;
+    int32_t lanes;
 } pvt_policy;
 
 /* Set the launch policy for later count calls on this dag (drops a recorded

@@ -30,7 +30,8 @@ class Stats(ctypes.Structure):
 class Policy(ctypes.Structure):
     """pvt_policy (include/pivoter.h)."""
     _fields_ = [("persistent", ctypes.c_int32), ("chunk", ctypes.c_int32), ("split", ctypes.c_int32 * 7),
-                ("graph", ctypes.c_int32), ("frames", ctypes.c_int32), ("wait_limit_us", ctypes.c_int32)]
+                ("graph", ctypes.c_int32), ("frames", ctypes.c_int32), ("wait_limit_us", ctypes.c_int32),
+                ("lanes", ctypes.c_int32)]
 
 
 class ServerConfig(ctypes.Structure):

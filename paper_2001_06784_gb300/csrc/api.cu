@@ -382,7 +382,7 @@ pvt_status pvt_dag_set_policy(pvt_dag *dag, const pvt_policy *policy)
     bool ok = dag && policy && (policy->persistent == 0 || policy->persistent == 1) && policy->chunk >= 1 &&
               policy->chunk <= 32 && (policy->graph == 0 || policy->graph == 1) &&
               (policy->frames == 0 || policy->frames == 1) && policy->wait_limit_us >= 0 &&
-              policy->wait_limit_us <= 1000000000;
+              policy->wait_limit_us <= 1000000000 && (policy->lanes == 0 || policy->lanes == 1);
     for (int c = 0; ok && c < NCLASS; ++c) ok = policy->split[c] == 0 || policy->split[c] == 1;
     if (!ok) {
         set_error("pvt_dag_set_policy: invalid argument");

@@ -211,9 +211,11 @@ static pvt_status ensure_binom(pvt_dag *g, int W, cudaStream_t s)
     return PVT_OK;
 }
 
-// Second phase of a two-phase global count (k_walk_frames) on stream s.
+// Second phase of a two-phase global count (k_walk_frames, or the lane walk)
+// on stream s.
 static pvt_status launch_frames(pvt_dag *g, const CountArgs &base, cudaStream_t s)
 {
+    if (g->policy.lanes) return launch_lanes_frames(g, base, s);
     CountArgs A = base;
     A.cls = FRAMES_SLOT;
     pvt_status st;
@@ -271,7 +273,11 @@ static pvt_status launch_all(pvt_dag *g, const CountArgs &A0, cudaStream_t s)
         cudaStream_t cs = serial ? s : g->side[c];
         if (!serial) PVT_CK(cudaStreamWaitEvent(cs, g->ev_fork, 0));
         switch (c) {
-            case 1: st = launch_class<1, MODE, MODE == MODE_GLOBAL>(g, A0, c, cs); break;
+            case 1:
+                st = MODE == MODE_GLOBAL && g->policy.lanes && g->policy.persistent
+                         ? launch_lanes_roots(g, A0, c, cs)
+                         : launch_class<1, MODE, MODE == MODE_GLOBAL>(g, A0, c, cs);
+                break;
             case 2: st = launch_class<2, MODE, MODE == MODE_GLOBAL>(g, A, c, cs); break;
             case 3: st = launch_class<4, MODE, MODE == MODE_GLOBAL>(g, A, c, cs); break;
             case 4: st = launch_class<8, MODE, MODE == MODE_GLOBAL>(g, A, c, cs); break;
@@ -633,9 +639,9 @@ pvt_status autotune(pvt_dag *g, int32_t kmax, int32_t W, uint64_t *C, cudaStream
         return PVT_EINVAL;
     }
     static const pvt_policy cand[3] = {
-        {1, 4, {0, 0, 1, 1, 1, 1, 1}, 0, 1, 0},
-        {1, 1, {0, 0, 0, 0, 0, 0, 0}, 0, 1, 0},
-        {1, 16, {0, 0, 1, 1, 1, 1, 1}, 0, 1, 0},
+        {1, 4, {0, 0, 1, 1, 1, 1, 1}, 0, 1, 0, 1},
+        {1, 1, {0, 0, 0, 0, 0, 0, 0}, 0, 1, 0, 1},
+        {1, 16, {0, 0, 1, 1, 1, 1, 1}, 0, 1, 0, 1},
     };
     const pvt_policy saved = g->policy;
     const bool saved_prof = g->profiling;
@@ -648,6 +654,7 @@ pvt_status autotune(pvt_dag *g, int32_t kmax, int32_t W, uint64_t *C, cudaStream
         for (int c = 0; c < 3 && st == PVT_OK; ++c) {
             g->policy = cand[c];
             g->policy.wait_limit_us = saved.wait_limit_us;
+            g->policy.lanes = saved.lanes;
             st = count_global(g, kmax, W, C, s);
             for (int cls = 1; st == PVT_OK && cls < NCLASS; ++cls) {
                 float x = 0.f;

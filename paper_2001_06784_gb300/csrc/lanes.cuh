@@ -1,0 +1,415 @@
+// One-word SCT walk with one subtree per lane (global counts).
+//
+// Labels of at most 32 members -- every root of the <= 32 out-degree class,
+// and the compacted subtrees that the wide walks emit as frames -- hold
+// almost all nodes of the SCT, and each of their nodes is a handful of
+// word operations: pivot selection is |S| ANDs and population counts on
+// one-word rows (Alg. 1 pivot step), each child one AND (Alg. 1 hold step).
+// A warp that walks one such subtree spends tens of instructions of
+// reductions, shuffles and stack bookkeeping per node.  Here each lane of a
+// warp walks its own subtree instead: the 32 one-word rows of lane j's label
+// sit in shared memory column j (rows[v][j]), its depth-first stack in
+// column j of the warp's stack arrays, so that every shared-memory access of
+// the warp touches 32 distinct banks whatever depth or row each lane is at.
+// Per node a lane runs the same steps as the warp walk -- pivot = most
+// neighbours inside S, ties to the lowest index; a clique label closes as
+// one leaf with p + |S|; children of at most two members close at once (the
+// closed forms of walk.cuh) -- so the tree, its statistics and the (h, p)
+// leaf histogram are exactly those of the warp walk.
+//
+// Work moves at three levels: a free lane takes the next item of the
+// launch's source (a frame, or a root whose adjacency it gathers itself); a
+// free lane with the source exhausted takes the oldest pending stack entry
+// of a busy lane of its warp (with that lane's rows); and, through the ring
+// queue of walk.cuh, a busy warp donates the oldest pending entry of its
+// most loaded lane, as a compacted frame, to a warp that has run dry.
+#pragma once
+
+#include "walk.cuh"
+
+namespace pvt {
+
+constexpr int LANE_WPB = 8;     // warps per block
+constexpr int LSTK = 32;        // per-lane stack slots (a label of s <= 32 keeps at most 31 pending)
+constexpr unsigned LANE_DONATE_EVERY = 32;  // node steps between looks at the ring queue
+
+struct LaneWork {
+    uint32_t rows[32][32];      // rows[v][lane]: row v of the lane's current subtree
+    uint32_t stkS[LSTK][32];    // pending labels, circular per lane
+    uint32_t stkHP[LSTK][32];   // their (h << 16) | p
+};
+
+// Per-lane walk statistics (each lane its own subtrees; summed at the end).
+struct LaneCounters {
+    unsigned long long nodes = 0, leaves = 0, words = 0;
+    __device__ __forceinline__ void flush(unsigned long long *stats, int slot, int lane)
+    {
+        const unsigned long long n = warp_sum64(nodes), l = warp_sum64(leaves), w = warp_sum64(words);
+        if (lane == 0 && n) {
+            atomicAdd(&stats[0], n);
+            atomicAdd(&stats[1], l);
+            atomicAdd(&stats[2], w);
+            if (slot >= 0) atomicAdd(&stats[3 + slot], w);
+        }
+    }
+    __device__ __forceinline__ static unsigned long long warp_sum64(unsigned long long x)
+    {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(FULL, x, o);
+        return x;
+    }
+};
+
+// Subtree of a label of at most two members in closed form, by one lane
+// (the cases of close_small in walk.cuh).
+template <bool SHIST>
+__device__ __forceinline__ void lane_close_small(unsigned long long *shist, const CountArgs &A, int cs,
+                                                 bool adjacent, int h, int p, LaneCounters &lc)
+{
+    const bool split = cs == 2 && !adjacent;
+    const bool hold = split && h + 1 <= A.kmax;
+    lc.nodes += 1 + split + hold;
+    lc.leaves += 1 + hold;
+    lc.words += (unsigned)cs;
+    if (!split) {
+        tally_lane<SHIST>(shist, A, h, p + cs);
+        return;
+    }
+    tally_lane<SHIST>(shist, A, h, p + 1);  // the pivot leaf below the pair
+    if (hold) tally_lane<SHIST>(shist, A, h + 1, p);
+}
+
+// One node of the lane's current subtree: label S reached with (h, p).
+// Leaves and closed forms clear `has`; otherwise hold children of three or
+// more members are pushed and the lane moves to the pivot child.
+template <bool SHIST>
+__device__ __forceinline__ void lane_node(LaneWork &L, unsigned long long *shist, const CountArgs &A, int lane,
+                                          uint32_t &S, int &h, int &p, bool &has, unsigned &top, unsigned bot,
+                                          LaneCounters &lc)
+{
+    const int s = __popc(S);
+    ++lc.nodes;
+    if (s == 0) {
+        ++lc.leaves;
+        tally_lane<SHIST>(shist, A, h, p);
+        has = false;
+        return;
+    }
+    // pivot: most neighbours inside S, ties -> lowest index; the degree sum
+    // tells whether S is a clique.  Two members per round for two
+    // independent load-AND-POPC chains.
+    uint32_t best = 0, dsum = 0, x = S;
+    while (x) {
+        const int v = __ffs(x) - 1;
+        x &= x - 1;
+        const uint32_t c = __popc(L.rows[v][lane] & S);
+        best = max(best, (c << 5) | (31u - (uint32_t)v));
+        dsum += c;
+        if (x) {
+            const int u = __ffs(x) - 1;
+            x &= x - 1;
+            const uint32_t c2 = __popc(L.rows[u][lane] & S);
+            best = max(best, (c2 << 5) | (31u - (uint32_t)u));
+            dsum += c2;
+        }
+    }
+    lc.words += (unsigned)s;
+    if (dsum == (uint32_t)s * (uint32_t)(s - 1)) {
+        ++lc.leaves;
+        tally_lane<SHIST>(shist, A, h, p + s);
+        has = false;
+        return;
+    }
+    const int piv = 31 - (int)(best & 31u);
+    const uint32_t rp = L.rows[piv][lane];
+    if (h + 1 <= A.kmax) {
+        // hold children N(S, v_i) minus the earlier non-neighbours, ascending
+        uint32_t y = S & ~rp & ~(1u << piv), below = 0;
+        while (y) {
+            const int v = __ffs(y) - 1;
+            y &= y - 1;
+            const uint32_t child = L.rows[v][lane] & S & ~below;
+            below |= 1u << v;
+            const int cs = __popc(child);
+            if (cs <= 2) {
+                const bool adj = cs == 2 && ((L.rows[__ffs(child) - 1][lane] >> (31 - __clz(child))) & 1u);
+                lane_close_small<SHIST>(shist, A, cs, adj, h + 1, p, lc);
+            } else {
+                L.stkS[top & (LSTK - 1)][lane] = child;
+                L.stkHP[top & (LSTK - 1)][lane] = ((uint32_t)(h + 1) << 16) | (uint32_t)p;
+                ++top;
+            }
+        }
+        if (top - bot > (unsigned)LSTK) atomicOr(A.err, DERR_STACK);  // cannot happen (at most 31 pending)
+    }
+    // the pivot child N(S, piv), closed at once if it has at most two members
+    const uint32_t P = rp & S;
+    const int ps = __popc(P);
+    if (ps <= 2) {
+        const bool adj = ps == 2 && ((L.rows[__ffs(P) - 1][lane] >> (31 - __clz(P))) & 1u);
+        lane_close_small<SHIST>(shist, A, ps, adj, h, p + 1, lc);
+        has = false;
+    } else {
+        S = P;
+        p += 1;
+    }
+}
+
+// Lanes of `freeM` without a source item take the oldest pending entry of a
+// busy lane (one that keeps work), with that lane's rows.  Returns the
+// lanes that received one.
+__device__ __forceinline__ unsigned lane_steal(LaneWork &L, int lane, unsigned freeM, uint32_t &S, int &h, int &p,
+                                               bool &has, unsigned top, unsigned &bot)
+{
+    const unsigned pend = top - bot;
+    const unsigned donors = __ballot_sync(FULL, pend >= 2 || (pend == 1 && has));
+    const int np = min(__popc(freeM), __popc(donors));
+    if (np == 0) return 0u;
+    const unsigned lt = (1u << lane) - 1u;
+    int src = lane;  // the donor this lane receives from
+    bool recv = false;
+    if ((freeM >> lane) & 1u) {
+        const int rank = __popc(freeM & lt);
+        if (rank < np) {
+            unsigned m = donors;  // the rank-th donor, counting from bit 0
+            for (int k = 0; k < rank; ++k) m &= m - 1;
+            src = __ffs(m) - 1;
+            recv = true;
+        }
+    }
+    const unsigned sbot = __shfl_sync(FULL, bot, src);
+    if (recv) {
+        S = L.stkS[sbot & (LSTK - 1)][src];
+        const uint32_t hp = L.stkHP[sbot & (LSTK - 1)][src];
+        h = (int)(hp >> 16);
+        p = (int)(hp & 0xFFFFu);
+        for (int v = 0; v < 32; ++v) L.rows[v][lane] = L.rows[v][src];
+        has = true;
+    }
+    if ((donors >> lane) & 1u) {
+        if (__popc(donors & lt) < np) ++bot;
+    }
+    __syncwarp();
+    return __ballot_sync(FULL, recv);
+}
+
+// Gather root r's induced adjacency into the lane's rows (lane-private: no
+// atomics).  Members 0..d-1 are N+(r) in ascending id; their ids sit in the
+// lane's (empty) stack column while it scans each member's out-list and
+// looks every entry up among them by binary search.  d <= 32.
+__device__ __forceinline__ void lane_gather(LaneWork &L, const CountArgs &A, int lane, uint32_t r, uint32_t &S,
+                                            unsigned *err)
+{
+    const int64_t rbeg = A.orow[r];
+    const int d = (int)(A.orow[r + 1] - rbeg);
+    if (d > 32 || d < 0) {
+        atomicOr(err, DERR_RANGE);
+        S = 0;
+        return;
+    }
+    for (int i = 0; i < d; ++i) {
+        L.stkS[i][lane] = A.ocol[rbeg + i];
+        L.rows[i][lane] = 0;
+    }
+    for (int i = 0; i < d; ++i) {
+        const uint32_t id = L.stkS[i][lane];
+        const int64_t b = A.orow[id], e = A.orow[id + 1];
+        for (int64_t t = b; t < e; t += 4) {
+            uint32_t xv[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) xv[q] = t + q < e ? A.ocol[t + q] : 0xFFFFFFFFu;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                if (t + q >= e) break;
+                int lo = 0, hi = d;
+                while (lo < hi) {
+                    const int mid = (lo + hi) >> 1;
+                    if (L.stkS[mid][lane] < xv[q]) lo = mid + 1; else hi = mid;
+                }
+                if (lo < d && L.stkS[lo][lane] == xv[q]) {
+                    L.rows[i][lane] |= 1u << lo;
+                    L.rows[lo][lane] |= 1u << i;
+                }
+            }
+        }
+    }
+    S = d >= 32 ? FULL : ((1u << d) - 1u);
+}
+
+// The lane walk over one source of items: the first `nitems` emitted frames
+// (ROOTS = false: A.emit) or the roots A.roots[0..nroots) (ROOTS = true).
+// Items are claimed through qctl[Q_ROOT]; qctl[Q_OUT] counts items not yet
+// finished (a warp returns its items once every lane is idle), and warps
+// that run dry wait on the ring queue for donated frames until it drops to
+// zero (walk.cuh: queue_take).
+template <bool SHIST, bool ROOTS>
+__device__ void lane_walk(LaneWork &L, unsigned long long *shist, const CountArgs &A, int lane, unsigned nitems,
+                          int slot)
+{
+    LaneCounters lc;
+    uint32_t S = 0;
+    int h = 0, p = 0;
+    bool has = false;
+    unsigned top = 0, bot = 0;
+    unsigned held = 0;      // items this warp took and has not returned (uniform)
+    bool src_done = false;  // uniform
+    unsigned steps = 0;
+    for (;;) {
+        unsigned freeM = __ballot_sync(FULL, !has && top == bot);
+        if (freeM) {
+            if (!src_done) {
+                const unsigned nf = __popc(freeM);
+                unsigned base = 0;
+                if (lane == 0) base = vload(A.qctl + Q_ROOT) < nitems ? atomicAdd(A.qctl + Q_ROOT, nf) : nitems;
+                base = __shfl_sync(FULL, base, 0);
+                const unsigned got = base >= nitems ? 0u : min(nf, nitems - base);
+                if (got < nf) src_done = true;
+                if (got) {
+                    // the first `got` free lanes take items base .. base+got-1
+                    const bool mine = ((freeM >> lane) & 1u) && (unsigned)__popc(freeM & ((1u << lane) - 1u)) < got;
+                    const unsigned item = base + (unsigned)__popc(freeM & ((1u << lane) - 1u));
+                    if (ROOTS) {
+                        if (mine) {
+                            lane_gather(L, A, lane, A.roots[item], S, A.err);
+                            h = 1;
+                            p = 0;
+                            has = true;
+                        }
+                    } else {
+                        unsigned m = freeM;
+#pragma unroll 4
+                        for (unsigned i = 0; i < got; ++i) {
+                            const int j = __ffs(m) - 1;
+                            m &= m - 1;
+                            const uint32_t *fr = A.emit + (size_t)(base + i) * FRAME_WORDS;
+                            L.rows[lane][j] = __ldcs(fr + 4 + lane);
+                        }
+                        if (mine) {
+                            const uint32_t *fr = A.emit + (size_t)item * FRAME_WORDS;
+                            const uint32_t hp = __ldcs(fr + 1);
+                            S = __ldcs(fr + 2);
+                            h = (int)(hp >> 16);
+                            p = (int)(hp & 0xFFFFu);
+                            has = true;
+                        }
+                    }
+                    held += got;
+                    __syncwarp();
+                }
+                freeM = __ballot_sync(FULL, !has && top == bot);
+            }
+            if (freeM && src_done) {
+                lane_steal(L, lane, freeM, S, h, p, has, top, bot);
+                freeM = __ballot_sync(FULL, !has && top == bot);
+            }
+            if (freeM == FULL) {
+                // every lane idle: return this warp's items, then wait for a
+                // donated frame (or the end of the launch)
+                if (lane == 0 && held) atomicSub(A.qctl + Q_OUT, held);
+                held = 0;
+                unsigned v = 0;
+                int kind = lane == 0 ? queue_take(A, 0u, v) : 0;
+                kind = __shfl_sync(FULL, kind, 0);
+                v = __shfl_sync(FULL, v, 0);
+                if (kind != 1) break;
+                const uint32_t *fr = A.qframes + (size_t)(v & (A.qcap - 1u)) * FRAME_WORDS;
+                L.rows[lane][0] = __ldcg(fr + 4 + lane);
+                uint32_t hp = 0, s0 = 0;
+                if (lane == 0) {
+                    hp = __ldcg(fr + 1);
+                    s0 = __ldcg(fr + 2);
+                }
+                __syncwarp();
+                if (lane == 0) {
+                    __threadfence();
+                    atomicExch(A.qdone + (v & (A.qcap - 1u)), v + 1u);
+                    S = s0;
+                    h = (int)(hp >> 16);
+                    p = (int)(hp & 0xFFFFu);
+                    has = true;
+                }
+                held = 1;
+                __syncwarp();
+                continue;
+            }
+        }
+        // one node per lane that has work
+        if (!has && top != bot) {
+            --top;
+            S = L.stkS[top & (LSTK - 1)][lane];
+            const uint32_t hp = L.stkHP[top & (LSTK - 1)][lane];
+            h = (int)(hp >> 16);
+            p = (int)(hp & 0xFFFFu);
+            has = true;
+        }
+        if (has) lane_node<SHIST>(L, shist, A, lane, S, h, p, has, top, bot, lc);
+        __syncwarp();
+        if (++steps % LANE_DONATE_EVERY == 0) {
+            // a warp waits on the ring: donate the oldest pending entry of the
+            // lane with the most pending entries, with that lane's rows
+            int hungry = lane == 0 ? (int)queue_hungry(A) : 0;
+            hungry = __shfl_sync(FULL, hungry, 0);
+            if (hungry) {
+                const unsigned pend = top - bot;
+                const unsigned key =
+                    pend >= 2 && __popc(L.stkS[bot & (LSTK - 1)][lane]) >= DONATE_MIN_COMPACT ? (pend << 5) | (unsigned)lane : 0u;
+                const unsigned best = __reduce_max_sync(FULL, key);
+                if (best) {
+                    const int dl = (int)(best & 31u);
+                    unsigned t = 0;
+                    uint32_t *fr = frame_reserve(A, lane, t);
+                    if (fr) {
+                        fr[4 + lane] = L.rows[lane][dl];
+                        if (lane == dl) {
+                            fr[0] = FRAME_COMPACT;
+                            fr[1] = L.stkHP[bot & (LSTK - 1)][lane];
+                            fr[2] = L.stkS[bot & (LSTK - 1)][lane];
+                            fr[3] = (uint32_t)A.cls;
+                            ++bot;
+                        }
+                        frame_publish(A, lane, t);
+                    }
+                }
+            }
+        }
+    }
+    lc.flush(A.stats, slot, lane);
+}
+
+template <bool SHIST>
+constexpr size_t lane_smem_bytes()
+{
+    return sizeof(LaneWork) * LANE_WPB + (SHIST ? sizeof(unsigned long long) * HIST_H * HIST_P : 0);
+}
+
+// ROOTS = false: every emitted compacted frame (A.emit, the count in
+// *A.emit_count capped at A.emit_cap), walk statistics to slot FRAMES_SLOT;
+// ROOTS = true: the roots A.roots[0..A.nroots) of the <= 32 class, slot A.cls.
+template <bool SHIST, bool ROOTS>
+__global__ void __launch_bounds__(32 * LANE_WPB, 2) k_lanes(CountArgs A)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    LaneWork *lw = reinterpret_cast<LaneWork *>(smem);
+    unsigned long long *shist = reinterpret_cast<unsigned long long *>(lw + LANE_WPB);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    unsigned nitems = A.nroots;
+    if (!ROOTS) {
+        const unsigned long long emitted = *(volatile unsigned long long *)A.emit_count;
+        nitems = (unsigned)min(emitted, (unsigned long long)A.emit_cap);
+        if (blockIdx.x == 0 && threadIdx.x == 0) A.stats[3 + NCLASS + 1] = emitted;
+    }
+    if (SHIST) {
+        for (int i = threadIdx.x; i < HIST_H * HIST_P; i += blockDim.x) shist[i] = 0;
+        __syncthreads();
+    }
+    lane_walk<SHIST, ROOTS>(lw[wid], shist, A, lane, nitems, ROOTS ? A.cls : NCLASS);
+    if (SHIST) {
+        __syncthreads();
+        for (int i = threadIdx.x; i < HIST_H * HIST_P; i += blockDim.x) {
+            const unsigned long long x = shist[i];
+            if (x) atomicAdd(&A.hist[(size_t)(i / HIST_P) * A.hstride + (i % HIST_P)], x);
+        }
+    }
+}
+
+}  // namespace pvt

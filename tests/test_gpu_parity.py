@@ -207,20 +207,23 @@ def test_repeat_calls_identical(pvt):
                                   lambda: graphs.clique_minus_random(200, 16, 2)])
 def test_policies_agree(pvt, make):
     """Plain (one warp per root) and persistent (work queue, split subtrees)
-    forms give identical words, and both match the oracle."""
+    forms, with one-word labels walked per warp or per lane, give identical
+    words and walk the same tree, and all match the oracle."""
     rp, col = make()
     ref = oracle.count(rp, col)
     dag = gpu_dag(pvt, rp, col)
     out = {}
     nosplit, mixed = (0,) * 7, (0, 0, 1, 0, 1, 0, 1)
     walked = {}
-    for persistent, chunk, split, frames in [(True, 4, None, True), (False, 1, None, False), (True, 1, nosplit, True),
-                                             (True, 32, mixed, True), (True, 4, None, False), (True, 1, nosplit, False)]:
-        dag.set_policy(persistent=persistent, chunk=chunk, split=split, frames=frames)
-        out[(persistent, chunk, split, frames)] = pvt.to_ints(dag.count_global(kmax=ref["kmax"]))
+    for form in [(True, 4, None, True, True), (False, 1, None, False, True), (True, 1, nosplit, True, True),
+                 (True, 32, mixed, True, True), (True, 4, None, False, True), (True, 1, nosplit, False, True),
+                 (True, 4, None, True, False), (True, 1, nosplit, True, False), (True, 4, None, False, False)]:
+        persistent, chunk, split, frames, lanes = form
+        dag.set_policy(persistent=persistent, chunk=chunk, split=split, frames=frames, lanes=lanes)
+        out[form] = pvt.to_ints(dag.count_global(kmax=ref["kmax"]))
         st = dag.stats()
         # the same tree whichever kernels walk it
-        walked[(persistent, chunk, split, frames)] = (st["sct_nodes"], st["sct_leaves"], st["pivot_words"])
+        walked[form] = (st["sct_nodes"], st["sct_leaves"], st["pivot_words"])
         assert sum(st["class_words"]) + st["frame_words"] == st["pivot_words"]
         if not (persistent and frames):
             assert st["frame_words"] == 0 and st["frames"] == 0
