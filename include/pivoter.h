@@ -292,6 +292,12 @@ pvt_status pvt_measure_popc_rate(double *pairs_per_s, void *stream);
  *               frames of the two-phase walk -- are walked one subtree per
  *               lane, 32 subtrees per warp, instead of one per warp; 0: one
  *               per warp.  The walked tree is the same either way.
+ *   cta[c]      per out-degree class c: 1 walks each root of the class with a
+ *               whole thread block over one shared copy of its adjacency
+ *               rows, the block's warps sharing its subtrees and walking its
+ *               labels of at most 32 members one per lane; 0: a warp per
+ *               root.  Global counts of the persistent form, classes above
+ *               128 (c >= 4) only.  Default {0, 0, 0, 0, 0, 1, 1}.
  * Each field is checked: PVT_EINVAL for a value out of range.
  */
 typedef struct pvt_policy {
@@ -302,6 +308,7 @@ typedef struct pvt_policy {
     int32_t frames;
     int32_t wait_limit_us;
     int32_t lanes;
+    int32_t cta[7];
 } pvt_policy;
 
 /* Set the launch policy for later count calls on this dag (drops a recorded

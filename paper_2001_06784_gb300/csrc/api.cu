@@ -384,6 +384,7 @@ pvt_status pvt_dag_set_policy(pvt_dag *dag, const pvt_policy *policy)
               (policy->frames == 0 || policy->frames == 1) && policy->wait_limit_us >= 0 &&
               policy->wait_limit_us <= 1000000000 && (policy->lanes == 0 || policy->lanes == 1);
     for (int c = 0; ok && c < NCLASS; ++c) ok = policy->split[c] == 0 || policy->split[c] == 1;
+    for (int c = 0; ok && c < NCLASS; ++c) ok = policy->cta[c] == 0 || (policy->cta[c] == 1 && c >= 4);
     if (!ok) {
         set_error("pvt_dag_set_policy: invalid argument");
         return PVT_EINVAL;

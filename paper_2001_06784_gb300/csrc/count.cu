@@ -279,10 +279,18 @@ static pvt_status launch_all(pvt_dag *g, const CountArgs &A0, cudaStream_t s)
                          : launch_class<1, MODE, MODE == MODE_GLOBAL>(g, A0, c, cs);
                 break;
             case 2: st = launch_class<2, MODE, MODE == MODE_GLOBAL>(g, A, c, cs); break;
+            case 4:
+            case 5:
+            case 6:
+                if (MODE == MODE_GLOBAL && g->policy.persistent && g->policy.cta[c]) {
+                    st = launch_cta_class(g, A, c, cs);
+                    break;
+                }
+                if (c == 4) st = launch_class<8, MODE, MODE == MODE_GLOBAL>(g, A, c, cs);
+                else if (c == 5) st = launch_class<16, MODE, MODE == MODE_GLOBAL>(g, A, c, cs);
+                else st = launch_class<32, MODE, MODE == MODE_GLOBAL>(g, A, c, cs);
+                break;
             case 3: st = launch_class<4, MODE, MODE == MODE_GLOBAL>(g, A, c, cs); break;
-            case 4: st = launch_class<8, MODE, MODE == MODE_GLOBAL>(g, A, c, cs); break;
-            case 5: st = launch_class<16, MODE, MODE == MODE_GLOBAL>(g, A, c, cs); break;
-            case 6: st = launch_class<32, MODE, MODE == MODE_GLOBAL>(g, A, c, cs); break;
         }
         if (!serial) PVT_CK(cudaEventRecord(g->ev_join[c], cs));
     }
@@ -639,9 +647,9 @@ pvt_status autotune(pvt_dag *g, int32_t kmax, int32_t W, uint64_t *C, cudaStream
         return PVT_EINVAL;
     }
     static const pvt_policy cand[3] = {
-        {1, 4, {0, 0, 1, 1, 1, 1, 1}, 0, 1, 0, 1},
-        {1, 1, {0, 0, 0, 0, 0, 0, 0}, 0, 1, 0, 1},
-        {1, 16, {0, 0, 1, 1, 1, 1, 1}, 0, 1, 0, 1},
+        {1, 4, {0, 0, 1, 1, 1, 1, 1}, 0, 1, 0, 1, {0, 0, 0, 0, 0, 0, 0}},
+        {1, 1, {0, 0, 0, 0, 0, 0, 0}, 0, 1, 0, 1, {0, 0, 0, 0, 1, 1, 1}},
+        {1, 16, {0, 0, 1, 1, 1, 1, 1}, 0, 1, 0, 1, {0, 0, 0, 0, 0, 0, 0}},
     };
     const pvt_policy saved = g->policy;
     const bool saved_prof = g->profiling;
@@ -673,9 +681,17 @@ pvt_status autotune(pvt_dag *g, int32_t kmax, int32_t W, uint64_t *C, cudaStream
         if (t[c][1] < t[bc][1]) bc = c;
     best.chunk = cand[bc].chunk;
     for (int cls = 0; cls < NCLASS; ++cls) {
+        best.cta[cls] = 0;
         if (cls < 2) { best.split[cls] = 0; continue; }
+        // candidate 1 walks the classes above 128 a block per root, the
+        // classes below a warp per root without splitting
         const float with = std::min(t[0][cls], t[2][cls]);
-        best.split[cls] = t[1][cls] < with ? 0 : 1;
+        if (t[1][cls] < with) {
+            best.split[cls] = 0;
+            best.cta[cls] = cls >= 4 ? 1 : 0;
+        } else {
+            best.split[cls] = 1;
+        }
     }
     g->policy = best;
     *chosen = best;

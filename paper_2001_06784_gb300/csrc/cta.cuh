@@ -1,0 +1,554 @@
+// CTA-per-root walk of the heaviest roots (global counts).
+//
+// A root of out-degree d keeps the adjacency induced on N+(r) as d rows of
+// ceil(d/32) words (step 1 of walk.cuh).  For d in the hundreds these rows
+// fill most of an SM's shared memory, so a kernel that gives each warp its
+// own root keeps a single warp per SM.  Here a thread block owns one root at
+// a time: its threads gather the rows together once, and all of its warps
+// walk that root's SCT (Alg. 1) over the one shared copy.  The warps share
+// the root's subtrees through a small queue in shared memory: a warp whose
+// subtree is done takes the next pending one, and busy warps hand over
+// their oldest pending subtree (the largest) while a warp of the block has
+// none.  Labels of at most 32 members leave the wide walk: they are
+// relabelled to one-word rows (the ballots of compact_rows in walk.cuh) into
+// a free lane of the warp's lane batch and walked one subtree per lane
+// (lanes.cuh), so the many small subtrees below a dense root never leave the
+// SM.  A warp runs its lanes whenever it has no wide work or no free lane.
+// The tree, its statistics and the (h, p) histogram are those of walk.cuh.
+#pragma once
+
+#include "lanes.cuh"
+
+namespace pvt {
+
+constexpr int CTA_QCAP = 32;                 // pending subtrees a block's queue holds
+constexpr int CTA_MAXW = 16;                 // warps per block at most
+constexpr unsigned CTA_DONATE_EVERY = 16;    // wide nodes between looks at the block's queue
+constexpr unsigned CTA_LANE_SLICE = 64;      // lane steps between looks while waiting
+constexpr unsigned long long CTA_LOCK_LIMIT_NS = 2000000000ull;  // 2 s for the block's queue lock
+
+// Shared state of a block, before the per-warp lane batches.
+template <int NW>
+struct alignas(16) CtaQueue {
+    int lock;
+    int head, tail;       // pending subtrees q[head .. tail)
+    int busy;             // warps walking a wide subtree of the current root
+    unsigned progress;    // bumped by every take and every finish (bounded waits)
+    unsigned root;        // index of the current root in the class list (~0: stop)
+    int d;                // its out-degree
+    uint32_t S[CTA_QCAP][NW];
+    uint32_t hp[CTA_QCAP];
+    // each warp's current label S and non-neighbour set R, for reads of word
+    // j by a loop index (registers hold them for the unrolled word loops)
+    uint32_t wS[CTA_MAXW][NW], wR[CTA_MAXW][NW];
+};
+
+template <int NW>
+struct CtaLayout {
+    static constexpr int RS = (NW & 1) ? NW : NW + 1;  // odd row stride: no bank conflicts
+    // dynamic shared memory: queue, per-warp lane batches, block histogram,
+    // then the root's rows (dmax rows of RS words)
+    static size_t bytes(int warps, int dmax)
+    {
+        return sizeof(CtaQueue<NW>) + sizeof(LaneWork) * warps + sizeof(unsigned long long) * HIST_H * HIST_P +
+               (size_t)dmax * RS * sizeof(uint32_t);
+    }
+    // the gather's member ids, offsets and out-list starts, laid over the
+    // lane batches of the first warps (idle during a gather)
+    static size_t gather_bytes(int dmax) { return (size_t)(2 * dmax + 2) * 4 + (size_t)dmax * 8; }
+};
+
+// The lane state of one lane (registers): its current subtree node and stack.
+struct LaneState {
+    uint32_t S = 0;
+    int h = 0, p = 0;
+    bool has = false;
+    unsigned top = 0, bot = 0;
+    __device__ __forceinline__ bool free_() const { return !has && top == bot; }
+};
+
+// Run the warp's lane batch: at most `budget` node steps, stopping early
+// once `stop_free` lanes are free (0: only when every lane is idle).
+template <bool SHIST>
+__device__ void lane_run(LaneWork &L, unsigned long long *shist, const CountArgs &A, int lane, LaneState &ls,
+                         LaneCounters &lc, unsigned budget, int stop_free)
+{
+    for (unsigned step = 0; step < budget; ++step) {
+        const unsigned freeM = __ballot_sync(FULL, ls.free_());
+        if (freeM == FULL) return;
+        if (stop_free && __popc(freeM) >= stop_free) return;
+        if (freeM) lane_steal(L, lane, freeM, ls.S, ls.h, ls.p, ls.has, ls.top, ls.bot);
+        if (!ls.has && ls.top != ls.bot) {
+            --ls.top;
+            ls.S = L.stkS[ls.top & (LSTK - 1)][lane];
+            const uint32_t hp = L.stkHP[ls.top & (LSTK - 1)][lane];
+            ls.h = (int)(hp >> 16);
+            ls.p = (int)(hp & 0xFFFFu);
+            ls.has = true;
+        }
+        if (ls.has) lane_node<SHIST>(L, shist, A, lane, ls.S, ls.h, ls.p, ls.has, ls.top, ls.bot, lc);
+        __syncwarp();
+    }
+}
+
+// Relabel the warp's current label (wS: NW-word bitset over the root's
+// members, s <= 32 of them) into a free lane of the batch: one-word rows,
+// member k of the label = its k-th member in ascending order.
+template <int NW, bool SHIST>
+__device__ __forceinline__ void lane_add(LaneWork &L, unsigned long long *shist, const CountArgs &A, int lane,
+                                         LaneState &ls, LaneCounters &lc, const uint32_t *adj, const uint32_t *wS,
+                                         int s, int h, int p)
+{
+    constexpr int RS = CtaLayout<NW>::RS;
+    unsigned freeM = __ballot_sync(FULL, ls.free_());
+    if (!freeM) {
+        lane_run<SHIST>(L, shist, A, lane, ls, lc, 0xFFFFFFFFu, 1);
+        freeM = __ballot_sync(FULL, ls.free_());
+    }
+    const int slot = __ffs(freeM) - 1;
+    // members in ascending order into the free lane's (empty) stack column
+    int before = 0;
+    for (int w = 0; w < NW; ++w) {
+        const uint32_t sw = wS[w];
+        if ((sw >> lane) & 1u) L.stkS[before + __popc(sw & ((1u << lane) - 1u))][slot] = (uint32_t)(w * 32 + lane);
+        before += __popc(sw);
+    }
+    __syncwarp();
+    const uint32_t mj = lane < s ? L.stkS[lane][slot] : 0u;
+    for (int k = 0; k < s; ++k) {
+        const uint32_t mk = L.stkS[k][slot];
+        const bool bit = lane < s && ((adj[mj * RS + (mk >> 5)] >> (mk & 31)) & 1u);
+        const uint32_t row = __ballot_sync(FULL, bit);
+        if (lane == 0) L.rows[k][slot] = row;
+    }
+    __syncwarp();
+    if (lane == slot) {
+        ls.S = s >= 32 ? FULL : ((1u << s) - 1u);
+        ls.h = h;
+        ls.p = p;
+        ls.has = true;
+        ls.top = ls.bot = 0;
+    }
+    __syncwarp();
+}
+
+// Block-wide lock of the queue (lane 0 of a warp), bounded.
+__device__ __forceinline__ bool cta_lock(int *lk, unsigned *err)
+{
+    const unsigned long long t0 = global_ns();
+    while (atomicCAS(lk, 0, 1) != 0) {
+        if (global_ns() - t0 > CTA_LOCK_LIMIT_NS) {
+            atomicOr(err, DERR_TIMEOUT);
+            return false;
+        }
+        __nanosleep(32);
+    }
+    __threadfence_block();
+    return true;
+}
+__device__ __forceinline__ void cta_unlock(int *lk)
+{
+    __threadfence_block();
+    atomicExch(lk, 0);
+}
+
+// Walk the wide subtree of the label in queue slot `qs` (NW words, > 32
+// members) depth first over the block's shared rows; pending children on
+// the warp's stack in global memory (at most d + 1 frames of NW + 1 words).
+// The caller holds the queue lock: the slot is copied out, then released.
+// The current label lives in registers S[w] (word loops are unrolled) and in
+// the warp's wS copy (reads of word j by loop index).
+template <int NW, bool SHIST>
+__device__ __forceinline__ void cta_dfs(CtaQueue<NW> &Q, LaneWork &L, unsigned long long *shist, const CountArgs &A,
+                                        int lane, int wid, LaneState &ls, LaneCounters &lc, WalkCounters &wc,
+                                        const uint32_t *adj, uint32_t *gstk, int qs, int d)
+{
+    constexpr int RS = CtaLayout<NW>::RS;
+    constexpr int FW = NW + 1;  // stack frame words: S, then (h << 16) | p
+    uint32_t *wS = Q.wS[wid], *wR = Q.wR[wid];
+    uint32_t S[NW];
+#pragma unroll
+    for (int w = 0; w < NW; ++w) S[w] = Q.S[qs][w];
+    const uint32_t hp0 = Q.hp[qs];
+    __syncwarp();
+    if (lane == 0) {
+        Q.progress += 1;
+        cta_unlock(&Q.lock);
+    }
+    int h = (int)(hp0 >> 16), p = (int)(hp0 & 0xFFFFu);
+    int top = 0, bot = 0;
+    unsigned clock = 0;
+    const uint32_t low = (1u << lane) - 1u;
+    const int warps = (int)(blockDim.x >> 5);
+    for (;;) {
+        int s = 0;
+#pragma unroll
+        for (int w = 0; w < NW; ++w) s += __popc(S[w]);
+#pragma unroll
+        for (int w = 0; w < NW; ++w)
+            if (lane == w) wS[w] = S[w];
+        __syncwarp();
+        bool closed = true;
+        if (s <= 32) {
+            lane_add<NW, SHIST>(L, shist, A, lane, ls, lc, adj, wS, s, h, p);
+        } else {
+            wc.nodes++;
+            ++clock;
+            // pivot: most neighbours inside S, ties -> lowest member index
+            uint32_t best = 0, dsum = 0;
+            for (int j = 0; j < NW; ++j) {
+                if ((wS[j] >> lane) & 1u) {
+                    const uint32_t *row = adj + (j * 32 + lane) * RS;
+                    uint32_t c = 0;
+#pragma unroll
+                    for (int w = 0; w < NW; ++w) c += __popc(row[w] & S[w]);
+                    best = max(best, ((c + 1u) << 10) | (1023u - (uint32_t)(j * 32 + lane)));
+                    dsum += c;
+                }
+            }
+            best = __reduce_max_sync(FULL, best);
+            dsum = __reduce_add_sync(FULL, dsum);
+            wc.words += (unsigned long long)s * NW;
+            const int piv = 1023 - (int)(best & 1023u);
+            if (dsum == (uint32_t)s * (uint32_t)(s - 1)) {
+                wc.leaves++;
+                tally_leaf<SHIST>(shist, A, lane, h, p + s);
+            } else {
+                const uint32_t *prow = adj + piv * RS;
+                uint32_t R[NW];
+                int nR = 0;
+#pragma unroll
+                for (int w = 0; w < NW; ++w) {
+                    R[w] = S[w] & ~prow[w];
+                    if (w == (piv >> 5)) R[w] &= ~(1u << (piv & 31));
+                    nR += __popc(R[w]);
+                }
+#pragma unroll
+                for (int w = 0; w < NW; ++w)
+                    if (lane == w) wR[w] = R[w];
+                __syncwarp();
+                if (nR > 0 && h + 1 <= A.kmax) {
+                    if (top + nR > d + 1) {
+                        if (bot > 0) {
+                            // donated frames left room at the base: move the live ones down
+                            for (int t = lane; t < (top - bot) * FW; t += 32) gstk[t] = gstk[bot * FW + t];
+                            top -= bot;
+                            bot = 0;
+                            __syncwarp();
+                        }
+                        if (top + nR > d + 1) {
+                            if (lane == 0) atomicOr(A.err, DERR_STACK);
+                            return;
+                        }
+                    }
+                    // hold child of member j*32+lane: N(S, v) minus the earlier
+                    // members of R; labels of at most two members close here
+                    int before = 0;
+                    for (int j = 0; j < NW; ++j) {
+                        const uint32_t Rj = wR[j];
+                        const bool inR = (Rj >> lane) & 1u;
+                        bool push = inR;
+                        const uint32_t *row = adj + (j * 32 + lane) * RS;
+                        if (inR) {
+                            int cs = 0, a = 0, b = 0;
+#pragma unroll
+                            for (int w = 0; w < NW; ++w) {
+                                const uint32_t bl = w < j ? R[w] : (w == j ? (Rj & low) : 0u);
+                                const uint32_t cw = row[w] & S[w] & ~bl;
+                                if (cw) {
+                                    if (cs == 0) a = w * 32 + __ffs(cw) - 1;
+                                    b = w * 32 + 31 - __clz(cw);
+                                }
+                                cs += __popc(cw);
+                            }
+                            if (cs <= 2) {
+                                const bool adjp = cs == 2 && ((adj[a * RS + (b >> 5)] >> (b & 31)) & 1u);
+                                close_small<SHIST, false>(shist, A, lane, cs, adjp, h + 1, p, NW, wc);
+                                push = false;
+                            }
+                        }
+                        const uint32_t pushed = __ballot_sync(FULL, push);
+                        if (push) {
+                            uint32_t *fr = gstk + (size_t)(top + before + __popc(pushed & low)) * FW;
+#pragma unroll
+                            for (int w = 0; w < NW; ++w) {
+                                const uint32_t bl = w < j ? R[w] : (w == j ? (Rj & low) : 0u);
+                                fr[w] = row[w] & S[w] & ~bl;
+                            }
+                            fr[NW] = ((uint32_t)(h + 1) << 16) | (uint32_t)p;
+                        }
+                        before += __popc(pushed);
+                    }
+                    top += before;
+                    __syncwarp();
+                    if (clock >= CTA_DONATE_EVERY) {
+                        clock = 0;
+                        // a warp of the block is not walking a wide subtree: hand
+                        // it our oldest pending one (the largest), if there is room
+                        int give = 0;
+                        if (lane == 0 && top - bot >= 2 && *(volatile int *)&Q.busy < warps &&
+                            *(volatile int *)&Q.tail - *(volatile int *)&Q.head < CTA_QCAP) {
+                            int sz = 0;
+                            for (int w = 0; w < NW; ++w) sz += __popc(gstk[bot * FW + w]);
+                            if (sz >= DONATE_MIN_WIDE && cta_lock(&Q.lock, A.err)) {
+                                give = 1;
+                                if (Q.tail - Q.head >= CTA_QCAP) {
+                                    cta_unlock(&Q.lock);
+                                    give = 0;
+                                }
+                            }
+                        }
+                        give = __shfl_sync(FULL, give, 0);
+                        if (give) {
+                            const int slot = Q.tail % CTA_QCAP;
+                            if (lane < NW) Q.S[slot][lane] = gstk[bot * FW + lane];
+                            if (lane == 0) Q.hp[slot] = gstk[bot * FW + NW];
+                            __syncwarp();
+                            if (lane == 0) {
+                                Q.tail += 1;
+                                Q.progress += 1;
+                                cta_unlock(&Q.lock);
+                            }
+                            ++bot;
+                        }
+                    }
+                }
+                // continue into the pivot child N(S, piv), or close it at once
+                int ps = 0, a = 0, b = 0;
+                uint32_t P[NW];
+#pragma unroll
+                for (int w = 0; w < NW; ++w) {
+                    P[w] = prow[w] & S[w];
+                    if (P[w]) {
+                        if (ps == 0) a = w * 32 + __ffs(P[w]) - 1;
+                        b = w * 32 + 31 - __clz(P[w]);
+                    }
+                    ps += __popc(P[w]);
+                }
+                if (ps <= 2) {
+                    const bool adjp = ps == 2 && ((adj[a * RS + (b >> 5)] >> (b & 31)) & 1u);
+                    close_small<SHIST, true>(shist, A, lane, ps, adjp, h, p + 1, NW, wc);
+                } else {
+                    closed = false;
+#pragma unroll
+                    for (int w = 0; w < NW; ++w) S[w] = P[w];
+                    p += 1;
+                }
+            }
+        }
+        __syncwarp();
+        if (!closed) continue;
+        if (top == bot) break;
+        --top;
+#pragma unroll
+        for (int w = 0; w < NW; ++w) S[w] = gstk[top * FW + w];
+        const uint32_t hp = gstk[top * FW + NW];
+        h = (int)(hp >> 16);
+        p = (int)(hp & 0xFFFFu);
+    }
+    __syncwarp();
+}
+
+// The block's rows for root r (all threads): member ids, their out-list
+// starts and the prefix offsets of their lengths in `scratch`, then every
+// entry of the members' out-lists looked up among the members by binary
+// search.  Q.d receives the out-degree (0 after a range error).
+template <int NW>
+__device__ void cta_gather(CtaQueue<NW> &Q, unsigned char *scratch, uint32_t *adj, const CountArgs &A, uint32_t r,
+                           int dmax)
+{
+    constexpr int RS = CtaLayout<NW>::RS;
+    const int64_t rbeg = A.orow[r];
+    const int d = (int)(A.orow[r + 1] - rbeg);
+    uint32_t *ids = reinterpret_cast<uint32_t *>(scratch);
+    uint32_t *off = ids + dmax;                                  // d + 1 prefix offsets
+    int64_t *rs = reinterpret_cast<int64_t *>(off + dmax + 2);   // 8-byte aligned: 2 dmax + 2 words before
+    const int tid = threadIdx.x, nt = blockDim.x;
+    __shared__ uint32_t wsum[32];
+    if (d > 32 * NW || d > dmax) {
+        if (tid == 0) {
+            atomicOr(A.err, DERR_RANGE);
+            Q.d = 0;
+        }
+        __syncthreads();
+        return;
+    }
+    for (int t = tid; t < d * RS; t += nt) adj[t] = 0;
+    // member i: id, out-list start, length; block scan of the lengths
+    const int lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
+    uint32_t carry = 0;
+    for (int i0 = 0; i0 < d; i0 += nt) {
+        const int i = i0 + tid;
+        uint32_t od = 0;
+        if (i < d) {
+            const uint32_t id = A.ocol[rbeg + i];
+            const int64_t b = A.orow[id];
+            od = (uint32_t)(A.orow[id + 1] - b);
+            ids[i] = id;
+            rs[i] = b;
+        }
+        uint32_t inc = od;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t t = __shfl_up_sync(FULL, inc, o);
+            if (lane >= o) inc += t;
+        }
+        if (lane == 31) wsum[wid] = inc;
+        __syncthreads();
+        if (wid == 0) {
+            uint32_t x = lane < nw ? wsum[lane] : 0u;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t t = __shfl_up_sync(FULL, x, o);
+                if (lane >= o) x += t;
+            }
+            if (lane < nw) wsum[lane] = x;
+        }
+        __syncthreads();
+        const uint32_t wbase = wid ? wsum[wid - 1] : 0u;
+        if (i < d) off[i + 1] = carry + wbase + inc;
+        carry += wsum[nw - 1];
+        __syncthreads();
+    }
+    if (tid == 0) {
+        off[0] = 0;
+        Q.d = d;
+    }
+    __syncthreads();
+    const uint32_t T = off[d];
+    for (uint32_t t = tid; t < T; t += nt) {
+        // member u owning entry t: the largest u with off[u] <= t
+        int lo = 0, hi = d;
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (off[mid] <= t) lo = mid; else hi = mid;
+        }
+        const uint32_t x = A.ocol[rs[lo] + (t - off[lo])];
+        int a = 0, b = d;
+        while (a < b) {
+            const int mid = (a + b) >> 1;
+            if (ids[mid] < x) a = mid + 1; else b = mid;
+        }
+        if (a < d && ids[a] == x) {
+            atomicOr(&adj[lo * RS + (a >> 5)], 1u << (a & 31));
+            atomicOr(&adj[a * RS + (lo >> 5)], 1u << (lo & 31));
+        }
+    }
+    __syncthreads();
+}
+
+// Persistent blocks over the roots A.roots[0..A.nroots) of one class: each
+// block takes a root, gathers it, and its warps walk the root's subtrees.
+// dmax: the largest out-degree of the class (rows and stacks are sized by it).
+template <int NW, bool SHIST>
+__global__ void __launch_bounds__(32 * CTA_MAXW, 1) k_cta(CountArgs A, int dmax)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    CtaQueue<NW> &Q = *reinterpret_cast<CtaQueue<NW> *>(smem);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, warps = blockDim.x >> 5;
+    LaneWork *lw = reinterpret_cast<LaneWork *>(smem + sizeof(CtaQueue<NW>));
+    unsigned long long *shist = reinterpret_cast<unsigned long long *>(lw + warps);
+    uint32_t *adj = reinterpret_cast<uint32_t *>(shist + HIST_H * HIST_P);
+    LaneWork &L = lw[wid];
+    uint32_t *gstk = A.gstack + (size_t)(blockIdx.x * warps + wid) * (size_t)(dmax + 1) * (NW + 1);
+    LaneState ls;
+    LaneCounters lc;
+    WalkCounters wc;
+    if (SHIST)
+        for (int i = threadIdx.x; i < HIST_H * HIST_P; i += blockDim.x) shist[i] = 0;
+    if (threadIdx.x == 0) Q.lock = 0;
+    __syncthreads();
+    for (;;) {
+        // ---- next root (one decision for the whole block)
+        if (threadIdx.x == 0) {
+            Q.root = (vload(A.err) & (DERR_STACK | DERR_RANGE | DERR_TIMEOUT)) ? 0xFFFFFFFFu : atomicAdd(A.qhead, 1u);
+            Q.head = Q.tail = Q.busy = 0;
+            Q.progress = 0;
+        }
+        __syncthreads();
+        const unsigned qi = Q.root;
+        if (qi >= A.nroots) break;
+        // the gather's scratch lies over the lane batches of the first warps:
+        // every lane batch is finished first
+        lane_run<SHIST>(L, shist, A, lane, ls, lc, 0xFFFFFFFFu, 0);
+        __syncthreads();
+        cta_gather<NW>(Q, reinterpret_cast<unsigned char *>(lw), adj, A, A.roots[qi], dmax);
+        const int d = Q.d;
+        if (threadIdx.x == 0 && d > 0) {
+#pragma unroll
+            for (int w = 0; w < NW; ++w) {
+                const int bits = d - 32 * w;
+                Q.S[0][w] = bits >= 32 ? FULL : (bits <= 0 ? 0u : ((1u << bits) - 1u));
+            }
+            Q.hp[0] = 1u << 16;  // h = 1 (the root's hold link), p = 0
+            Q.tail = 1;
+        }
+        __syncthreads();
+        // ---- walk the root: take pending subtrees until none is left and no
+        // warp can make more
+        unsigned last = 0xFFFFFFFFu;
+        unsigned long long t0 = global_ns();
+        for (;;) {
+            int took = 0;
+            if (lane == 0) {
+                if (*(volatile int *)&Q.tail > *(volatile int *)&Q.head) {
+                    if (cta_lock(&Q.lock, A.err)) {
+                        if (Q.tail > Q.head) {
+                            took = 1 + (Q.head % CTA_QCAP);
+                            Q.head += 1;
+                            Q.busy += 1;  // lock released by cta_dfs once the slot is copied
+                        } else {
+                            cta_unlock(&Q.lock);
+                        }
+                    } else {
+                        took = -1;  // timed out (status set)
+                    }
+                } else if (*(volatile int *)&Q.busy == 0) {
+                    took = -1;  // the root is done
+                }
+            }
+            took = __shfl_sync(FULL, took, 0);
+            if (took < 0) break;
+            if (took > 0) {
+                cta_dfs<NW, SHIST>(Q, L, shist, A, lane, wid, ls, lc, wc, adj, gstk, took - 1, d);
+                wc.fold();
+                __syncwarp();
+                if (lane == 0) {
+                    atomicSub(&Q.busy, 1);
+                    atomicAdd(&Q.progress, 1u);
+                }
+                t0 = global_ns();
+                continue;
+            }
+            // nothing to take yet: run the lane batch a little, then look again
+            if (__ballot_sync(FULL, ls.free_()) != FULL) {
+                lane_run<SHIST>(L, shist, A, lane, ls, lc, CTA_LANE_SLICE, 0);
+                t0 = global_ns();
+            } else {
+                const unsigned pr = *(volatile unsigned *)&Q.progress;
+                if (pr != last) {
+                    last = pr;
+                    t0 = global_ns();
+                } else if (global_ns() - t0 > A.idle_ns) {
+                    if (lane == 0) atomicOr(A.err, DERR_TIMEOUT);
+                    break;
+                }
+                __nanosleep(128);
+            }
+        }
+        __syncthreads();
+    }
+    // ---- every root taken: finish the lane batch
+    lane_run<SHIST>(L, shist, A, lane, ls, lc, 0xFFFFFFFFu, 0);
+    wc.flush(A.stats, A.cls, lane);
+    lc.flush(A.stats, A.cls, lane);
+    if (SHIST) {
+        __syncthreads();
+        for (int i = threadIdx.x; i < HIST_H * HIST_P; i += blockDim.x) {
+            const unsigned long long x = shist[i];
+            if (x) atomicAdd(&A.hist[(size_t)(i / HIST_P) * A.hstride + (i % HIST_P)], x);
+        }
+    }
+}
+
+}  // namespace pvt

@@ -1104,6 +1104,8 @@ constexpr unsigned SPLIT_QCAP = 1u << 17;
 // out-degree class cls (<= 32), and the frames of the two-phase count.
 pvt_status launch_lanes_roots(pvt_dag *g, const CountArgs &base, int cls, cudaStream_t s);
 pvt_status launch_lanes_frames(pvt_dag *g, const CountArgs &base, cudaStream_t s);
+// The CTA-per-root walk (cta.cuh, walk_cta.cu) of out-degree class cls >= 4.
+pvt_status launch_cta_class(pvt_dag *g, const CountArgs &base, int cls, cudaStream_t s);
 
 template <int NW, int MODE, bool SHIST>
 pvt_status launch_class(pvt_dag *g, const CountArgs &base, int cls, cudaStream_t s)

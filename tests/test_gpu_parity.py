@@ -207,19 +207,23 @@ def test_repeat_calls_identical(pvt):
                                   lambda: graphs.clique_minus_random(200, 16, 2)])
 def test_policies_agree(pvt, make):
     """Plain (one warp per root) and persistent (work queue, split subtrees)
-    forms, with one-word labels walked per warp or per lane, give identical
-    words and walk the same tree, and all match the oracle."""
+    forms, with one-word labels walked per warp or per lane and the classes
+    above 128 walked a warp or a block per root, give identical words and
+    walk the same tree, and all match the oracle."""
     rp, col = make()
     ref = oracle.count(rp, col)
     dag = gpu_dag(pvt, rp, col)
     out = {}
     nosplit, mixed = (0,) * 7, (0, 0, 1, 0, 1, 0, 1)
     walked = {}
-    for form in [(True, 4, None, True, True), (False, 1, None, False, True), (True, 1, nosplit, True, True),
-                 (True, 32, mixed, True, True), (True, 4, None, False, True), (True, 1, nosplit, False, True),
-                 (True, 4, None, True, False), (True, 1, nosplit, True, False), (True, 4, None, False, False)]:
-        persistent, chunk, split, frames, lanes = form
-        dag.set_policy(persistent=persistent, chunk=chunk, split=split, frames=frames, lanes=lanes)
+    nocta, allcta = (0,) * 7, (0, 0, 0, 0, 1, 1, 1)
+    for form in [(True, 4, None, True, True, None), (False, 1, None, False, True, None),
+                 (True, 1, nosplit, True, True, nocta), (True, 32, mixed, True, True, allcta),
+                 (True, 4, None, False, True, allcta), (True, 1, nosplit, False, True, None),
+                 (True, 4, None, True, False, nocta), (True, 1, nosplit, True, False, allcta),
+                 (True, 4, None, False, False, nocta)]:
+        persistent, chunk, split, frames, lanes, cta = form
+        dag.set_policy(persistent=persistent, chunk=chunk, split=split, frames=frames, lanes=lanes, cta=cta)
         out[form] = pvt.to_ints(dag.count_global(kmax=ref["kmax"]))
         st = dag.stats()
         # the same tree whichever kernels walk it
