@@ -298,6 +298,10 @@ pvt_status pvt_measure_popc_rate(double *pairs_per_s, void *stream);
  *               labels of at most 32 members one per lane; 0: a warp per
  *               root.  Global counts of the persistent form, classes above
  *               128 (c >= 4) only.  Default {0, 0, 0, 0, 0, 1, 1}.
+ *   serial      0 (default): the classes' kernels run on streams of their own
+ *               and overlap; 1: one after another on the caller's stream, so
+ *               that the phase times of pvt_dag_stats are each kernel's own
+ *               (a measurement setting; results are the same).
  * Each field is checked: PVT_EINVAL for a value out of range.
  */
 typedef struct pvt_policy {
@@ -309,6 +313,7 @@ typedef struct pvt_policy {
     int32_t wait_limit_us;
     int32_t lanes;
     int32_t cta[7];
+    int32_t serial;
 } pvt_policy;
 
 /* Set the launch policy for later count calls on this dag (drops a recorded

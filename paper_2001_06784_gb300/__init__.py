@@ -151,10 +151,10 @@ class Dag:
         _lib.check(_lib.lib().pvt_dag_get_policy(self._h, ctypes.byref(pol)))
         return dict(persistent=bool(pol.persistent), chunk=pol.chunk, split=list(pol.split), graph=bool(pol.graph),
                     frames=bool(pol.frames), wait_limit_us=pol.wait_limit_us, lanes=bool(pol.lanes),
-                    cta=list(pol.cta))
+                    cta=list(pol.cta), serial=bool(pol.serial))
 
     def set_policy(self, persistent: bool = True, chunk: int = 4, split=None, graph: bool = False,
-                   frames: bool = True, wait_limit_us: int = 0, lanes: bool = True, cta=None):
+                   frames: bool = True, wait_limit_us: int = 0, lanes: bool = True, cta=None, serial: bool = False):
         """Launch policy of the walk kernels: persistent warps with a device
         work queue (default) or the plain one-warp-per-root form; per
         out-degree class whether heavy roots split across warps (7 flags,
@@ -164,13 +164,15 @@ class Dag:
         wait_limit_us > 0 shortens the bounded device waits (a test of the
         PVT_ETIMEOUT path); whether one-word labels of global counts are
         walked one subtree per lane (lanes) or one per warp; per out-degree
-        class whether a thread block walks each root (cta, classes 4..6)."""
+        class whether a thread block walks each root (cta, classes 4..6);
+        serial runs the classes one after another (isolated phase times)."""
         split = [0, 0, 1, 1, 1, 1, 1] if split is None else [int(x) for x in split]
         cta = [0, 0, 0, 0, 0, 1, 1] if cta is None else [int(x) for x in cta]
         if len(split) != 7 or len(cta) != 7:
             raise ValueError("split and cta need one flag per out-degree class (7)")
         pol = _lib.Policy(1 if persistent else 0, int(chunk), (ctypes.c_int32 * 7)(*split), 1 if graph else 0,
-                          1 if frames else 0, int(wait_limit_us), 1 if lanes else 0, (ctypes.c_int32 * 7)(*cta))
+                          1 if frames else 0, int(wait_limit_us), 1 if lanes else 0, (ctypes.c_int32 * 7)(*cta),
+                          1 if serial else 0)
         _lib.check(_lib.lib().pvt_dag_set_policy(self._h, ctypes.byref(pol)))
 
     def autotune(self, kmax=None, W=None, out=None, stream=None):
@@ -186,7 +188,7 @@ class Dag:
                                                ms.ctypes.data))
         return (dict(persistent=bool(pol.persistent), chunk=pol.chunk, split=list(pol.split),
                      graph=bool(pol.graph), frames=bool(pol.frames), wait_limit_us=pol.wait_limit_us,
-                     lanes=bool(pol.lanes), cta=list(pol.cta)), ms, out)
+                     lanes=bool(pol.lanes), cta=list(pol.cta), serial=bool(pol.serial)), ms, out)
 
     def set_profiling(self, on: bool):
         _lib.check(_lib.lib().pvt_dag_set_profiling(self._h, 1 if on else 0))

@@ -31,7 +31,7 @@ class Policy(ctypes.Structure):
     """pvt_policy (include/pivoter.h)."""
     _fields_ = [("persistent", ctypes.c_int32), ("chunk", ctypes.c_int32), ("split", ctypes.c_int32 * 7),
                 ("graph", ctypes.c_int32), ("frames", ctypes.c_int32), ("wait_limit_us", ctypes.c_int32),
-                ("lanes", ctypes.c_int32), ("cta", ctypes.c_int32 * 7)]
+                ("lanes", ctypes.c_int32), ("cta", ctypes.c_int32 * 7), ("serial", ctypes.c_int32)]
 
 
 class ServerConfig(ctypes.Structure):

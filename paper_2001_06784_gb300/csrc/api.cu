@@ -385,6 +385,7 @@ pvt_status pvt_dag_set_policy(pvt_dag *dag, const pvt_policy *policy)
               policy->wait_limit_us <= 1000000000 && (policy->lanes == 0 || policy->lanes == 1);
     for (int c = 0; ok && c < NCLASS; ++c) ok = policy->split[c] == 0 || policy->split[c] == 1;
     for (int c = 0; ok && c < NCLASS; ++c) ok = policy->cta[c] == 0 || (policy->cta[c] == 1 && c >= 4);
+    ok = ok && (policy->serial == 0 || policy->serial == 1);
     if (!ok) {
         set_error("pvt_dag_set_policy: invalid argument");
         return PVT_EINVAL;

@@ -266,7 +266,7 @@ static pvt_status launch_all(pvt_dag *g, const CountArgs &A0, cudaStream_t s)
     }
     // heavy classes on side streams so that they overlap the light ones (or
     // all on s, one after another, when the autotuner times them)
-    const bool serial = g->serial;
+    const bool serial = g->serial || g->policy.serial;
     if (!serial) PVT_CK(cudaEventRecord(g->ev_fork, s));
     pvt_status st = PVT_OK;
     for (int c = NCLASS - 1; c >= 1 && st == PVT_OK; --c) {
@@ -456,7 +456,7 @@ pvt_status count_global(pvt_dag *g, int32_t kmax, int32_t W, uint64_t *C, cudaSt
     pvt_status st = check_args(g, kmax, W, C, 1, "pvt_count_global");
     if (st != PVT_OK) return st;
     begin_call(g);
-    const bool use_graph = g->policy.graph != 0 && !g->serial;
+    const bool use_graph = g->policy.graph != 0 && !g->serial && !g->policy.serial;
     g->hist_valid = false;
     if (use_graph && g->graph_exec && g->graph_kmax == kmax && g->graph_W == W && g->graph_out == C) {
         PVT_CK(cudaGraphLaunch(g->graph_exec, s));
@@ -647,9 +647,9 @@ pvt_status autotune(pvt_dag *g, int32_t kmax, int32_t W, uint64_t *C, cudaStream
         return PVT_EINVAL;
     }
     static const pvt_policy cand[3] = {
-        {1, 4, {0, 0, 1, 1, 1, 1, 1}, 0, 1, 0, 1, {0, 0, 0, 0, 0, 0, 0}},
-        {1, 1, {0, 0, 0, 0, 0, 0, 0}, 0, 1, 0, 1, {0, 0, 0, 0, 1, 1, 1}},
-        {1, 16, {0, 0, 1, 1, 1, 1, 1}, 0, 1, 0, 1, {0, 0, 0, 0, 0, 0, 0}},
+        {1, 4, {0, 0, 1, 1, 1, 1, 1}, 0, 1, 0, 1, {0, 0, 0, 0, 0, 0, 0}, 0},
+        {1, 1, {0, 0, 0, 0, 0, 0, 0}, 0, 1, 0, 1, {0, 0, 0, 0, 1, 1, 1}, 0},
+        {1, 16, {0, 0, 1, 1, 1, 1, 1}, 0, 1, 0, 1, {0, 0, 0, 0, 0, 0, 0}, 0},
     };
     const pvt_policy saved = g->policy;
     const bool saved_prof = g->profiling;

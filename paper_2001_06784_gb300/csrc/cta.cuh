@@ -21,9 +21,10 @@
 
 namespace pvt {
 
-constexpr int CTA_QCAP = 32;                 // pending subtrees a block's queue holds
+constexpr int CTA_QCAP = 32;                 // pending wide subtrees a block's queue holds
+constexpr int CTA_CQCAP = 64;                // relabelled small subtrees it holds
 constexpr int CTA_MAXW = 16;                 // warps per block at most
-constexpr unsigned CTA_DONATE_EVERY = 16;    // wide nodes between looks at the block's queue
+constexpr unsigned CTA_DONATE_EVERY = 2;     // wide nodes between looks at the block's queue
 constexpr unsigned CTA_LANE_SLICE = 64;      // lane steps between looks while waiting
 constexpr unsigned long long CTA_LOCK_LIMIT_NS = 2000000000ull;  // 2 s for the block's queue lock
 
@@ -31,16 +32,22 @@ constexpr unsigned long long CTA_LOCK_LIMIT_NS = 2000000000ull;  // 2 s for the 
 template <int NW>
 struct alignas(16) CtaQueue {
     int lock;
-    int head, tail;       // pending subtrees q[head .. tail)
+    int head, tail;       // pending wide subtrees q[head .. tail)
     int busy;             // warps walking a wide subtree of the current root
     unsigned progress;    // bumped by every take and every finish (bounded waits)
     unsigned root;        // index of the current root in the class list (~0: stop)
     int d;                // its out-degree
+    int chead, ctail;     // relabelled small subtrees taken / reserved
     uint32_t S[CTA_QCAP][NW];
     uint32_t hp[CTA_QCAP];
+    // relabelled small subtrees: one-word rows, label, (h, p); an entry t is
+    // published when cseq[t % CTA_CQCAP] == t + 1
+    uint32_t crow[CTA_CQCAP][33];  // odd stride: takers of different entries hit distinct banks
+    uint32_t cS[CTA_CQCAP], chp[CTA_CQCAP], cseq[CTA_CQCAP];
     // each warp's current label S and non-neighbour set R, for reads of word
     // j by a loop index (registers hold them for the unrolled word loops)
     uint32_t wS[CTA_MAXW][NW], wR[CTA_MAXW][NW];
+    uint32_t wM[CTA_MAXW][32];  // the members of a small label being relabelled
 };
 
 template <int NW>
@@ -48,14 +55,14 @@ struct CtaLayout {
     static constexpr int RS = (NW & 1) ? NW : NW + 1;  // odd row stride: no bank conflicts
     // dynamic shared memory: queue, per-warp lane batches, block histogram,
     // then the root's rows (dmax rows of RS words)
-    static size_t bytes(int warps, int dmax)
+    __host__ __device__ static size_t bytes(int warps, int dmax)
     {
-        return sizeof(CtaQueue<NW>) + sizeof(LaneWork) * warps + sizeof(unsigned long long) * HIST_H * HIST_P +
+        return sizeof(CtaQueue<NW>) + sizeof(LaneWork) * warps + sizeof(unsigned) * HIST_H * HIST_P +
                (size_t)dmax * RS * sizeof(uint32_t);
     }
-    // the gather's member ids, offsets and out-list starts, laid over the
-    // lane batches of the first warps (idle during a gather)
-    static size_t gather_bytes(int dmax) { return (size_t)(2 * dmax + 2) * 4 + (size_t)dmax * 8; }
+    // global scratch of a block's gather: member ids, prefix offsets (dmax + 2
+    // words) and out-list starts (dmax 8-byte words)
+    __host__ __device__ static size_t gather_words(int dmax) { return (size_t)(2 * dmax + 2) + 2 * (size_t)dmax; }
 };
 
 // The lane state of one lane (registers): its current subtree node and stack.
@@ -67,10 +74,36 @@ struct LaneState {
     __device__ __forceinline__ bool free_() const { return !has && top == bot; }
 };
 
+// The subtree of a label of at most two members in closed form (the cases
+// of close_small in walk.cuh), tallied in the block's 32-bit histogram.
+// UNIFORM: every lane calls with the same arguments, lane 0 tallies.
+template <bool UNIFORM>
+__device__ __forceinline__ void cta_close_small(unsigned *sh32, const CountArgs &A, int lane, int cs, bool adjacent,
+                                                int h, int p, unsigned wpm, WalkCounters &wc)
+{
+    const bool split = cs == 2 && !adjacent;
+    const bool hold = split && h + 1 <= A.kmax;
+    if (UNIFORM) {
+        wc.nodes += 1 + split + hold;
+        wc.leaves += 1 + hold;
+        wc.words += (unsigned long long)cs * wpm;
+    } else {
+        wc.xnodes += 1u + split + hold;
+        wc.xleaves += 1u + hold;
+        wc.xwords += (unsigned)cs * wpm;
+    }
+    if (UNIFORM && lane != 0) return;
+    if (!split) {
+        lane_tally(sh32, A, h, p + cs);
+        return;
+    }
+    lane_tally(sh32, A, h, p + 1);  // the pivot leaf below the pair
+    if (hold) lane_tally(sh32, A, h + 1, p);
+}
+
 // Run the warp's lane batch: at most `budget` node steps, stopping early
 // once `stop_free` lanes are free (0: only when every lane is idle).
-template <bool SHIST>
-__device__ void lane_run(LaneWork &L, unsigned long long *shist, const CountArgs &A, int lane, LaneState &ls,
+__device__ void lane_run(LaneWork &L, unsigned *sh32, const CountArgs &A, int lane, LaneState &ls,
                          LaneCounters &lc, unsigned budget, int stop_free)
 {
     for (unsigned step = 0; step < budget; ++step) {
@@ -86,41 +119,51 @@ __device__ void lane_run(LaneWork &L, unsigned long long *shist, const CountArgs
             ls.p = (int)(hp & 0xFFFFu);
             ls.has = true;
         }
-        if (ls.has) lane_node<SHIST>(L, shist, A, lane, ls.S, ls.h, ls.p, ls.has, ls.top, ls.bot, lc);
+        if (ls.has) lane_node(L, sh32, A, lane, ls.S, ls.h, ls.p, ls.has, ls.top, ls.bot, lc);
         __syncwarp();
     }
 }
 
 // Relabel the warp's current label (wS: NW-word bitset over the root's
-// members, s <= 32 of them) into a free lane of the batch: one-word rows,
-// member k of the label = its k-th member in ascending order.
-template <int NW, bool SHIST>
-__device__ __forceinline__ void lane_add(LaneWork &L, unsigned long long *shist, const CountArgs &A, int lane,
-                                         LaneState &ls, LaneCounters &lc, const uint32_t *adj, const uint32_t *wS,
-                                         int s, int h, int p)
+// members, s <= 32 of them): member k of the label = its k-th member in
+// ascending order; lane k returns row k of the one-word adjacency (the
+// ballot over lanes j of "member k is adjacent to member j").
+template <int NW>
+__device__ __forceinline__ uint32_t relabel_small(const uint32_t *adj, const uint32_t *wS, uint32_t *wM, int lane,
+                                                  int s)
 {
     constexpr int RS = CtaLayout<NW>::RS;
-    unsigned freeM = __ballot_sync(FULL, ls.free_());
-    if (!freeM) {
-        lane_run<SHIST>(L, shist, A, lane, ls, lc, 0xFFFFFFFFu, 1);
-        freeM = __ballot_sync(FULL, ls.free_());
-    }
-    const int slot = __ffs(freeM) - 1;
-    // members in ascending order into the free lane's (empty) stack column
     int before = 0;
     for (int w = 0; w < NW; ++w) {
         const uint32_t sw = wS[w];
-        if ((sw >> lane) & 1u) L.stkS[before + __popc(sw & ((1u << lane) - 1u))][slot] = (uint32_t)(w * 32 + lane);
+        if ((sw >> lane) & 1u) wM[before + __popc(sw & ((1u << lane) - 1u))] = (uint32_t)(w * 32 + lane);
         before += __popc(sw);
     }
     __syncwarp();
-    const uint32_t mj = lane < s ? L.stkS[lane][slot] : 0u;
+    const uint32_t mj = lane < s ? wM[lane] : 0u;
+    uint32_t mine = 0;
     for (int k = 0; k < s; ++k) {
-        const uint32_t mk = L.stkS[k][slot];
+        const uint32_t mk = __shfl_sync(FULL, mj, k);
         const bool bit = lane < s && ((adj[mj * RS + (mk >> 5)] >> (mk & 31)) & 1u);
         const uint32_t row = __ballot_sync(FULL, bit);
-        if (lane == 0) L.rows[k][slot] = row;
+        if (lane == k) mine = row;
     }
+    __syncwarp();
+    return mine;
+}
+
+// A relabelled small label into a free lane of the warp's own batch (run
+// the batch until a lane is free first).
+__device__ __forceinline__ void lane_add(LaneWork &L, unsigned *sh32, const CountArgs &A, int lane, LaneState &ls,
+                                         LaneCounters &lc, uint32_t row, int s, int h, int p)
+{
+    unsigned freeM = __ballot_sync(FULL, ls.free_());
+    if (!freeM) {
+        lane_run(L, sh32, A, lane, ls, lc, 0xFFFFFFFFu, 1);
+        freeM = __ballot_sync(FULL, ls.free_());
+    }
+    const int slot = __ffs(freeM) - 1;
+    L.rows[lane][slot] = row;
     __syncwarp();
     if (lane == slot) {
         ls.S = s >= 32 ? FULL : ((1u << s) - 1u);
@@ -152,14 +195,86 @@ __device__ __forceinline__ void cta_unlock(int *lk)
     atomicExch(lk, 0);
 }
 
+// A small label (s <= 32 members) found by a wide walk: relabelled into the
+// block's ring, from which any warp with free lanes takes it; into the
+// warp's own batch when the ring is full.
+template <int NW>
+__device__ __forceinline__ void cta_push_small(CtaQueue<NW> &Q, LaneWork &L, unsigned *sh32, const CountArgs &A,
+                                               int lane, int wid, LaneState &ls, LaneCounters &lc,
+                                               const uint32_t *adj, int s, int h, int p)
+{
+    const uint32_t row = relabel_small<NW>(adj, Q.wS[wid], Q.wM[wid], lane, s);
+    int t = -1;
+    if (lane == 0 && *(volatile int *)&Q.ctail - *(volatile int *)&Q.chead < CTA_CQCAP && cta_lock(&Q.lock, A.err)) {
+        if (Q.ctail - Q.chead < CTA_CQCAP) t = Q.ctail++;
+        cta_unlock(&Q.lock);
+    }
+    t = __shfl_sync(FULL, t, 0);
+    if (t < 0) {
+        lane_add(L, sh32, A, lane, ls, lc, row, s, h, p);
+        return;
+    }
+    const int e = t % CTA_CQCAP;
+    Q.crow[e][lane] = row;
+    if (lane == 0) {
+        Q.cS[e] = s >= 32 ? FULL : ((1u << s) - 1u);
+        Q.chp[e] = ((uint32_t)h << 16) | (uint32_t)p;
+    }
+    __syncwarp();
+    if (lane == 0) {
+        __threadfence_block();
+        *(volatile uint32_t *)&Q.cseq[e] = (uint32_t)t + 1u;
+    }
+}
+
+// Free lanes of the warp take published small labels from the block's ring
+// (copied out under the lock, so a slot is reused only once copied).
+// Returns how many were taken.
+template <int NW>
+__device__ __forceinline__ int cta_take_small(CtaQueue<NW> &Q, LaneWork &L, int lane, LaneState &ls, unsigned *err)
+{
+    const unsigned freeM = __ballot_sync(FULL, ls.free_());
+    if (!freeM) return 0;
+    int base = 0, n = 0;
+    if (lane == 0 && *(volatile int *)&Q.ctail > *(volatile int *)&Q.chead && cta_lock(&Q.lock, err)) {
+        base = Q.chead;
+        const int lim = min(__popc(freeM), Q.ctail - Q.chead);
+        while (n < lim && *(volatile uint32_t *)&Q.cseq[(base + n) % CTA_CQCAP] == (uint32_t)(base + n) + 1u) ++n;
+        if (n == 0) cta_unlock(&Q.lock);
+    }
+    n = __shfl_sync(FULL, n, 0);
+    if (n == 0) return 0;
+    base = __shfl_sync(FULL, base, 0);
+    __threadfence_block();
+    const int rank = __popc(freeM & ((1u << lane) - 1u));
+    if (((freeM >> lane) & 1u) && rank < n) {
+        const int e = (base + rank) % CTA_CQCAP;
+        for (int v = 0; v < 32; ++v) L.rows[v][lane] = Q.crow[e][v];
+        ls.S = Q.cS[e];
+        const uint32_t hp = Q.chp[e];
+        ls.h = (int)(hp >> 16);
+        ls.p = (int)(hp & 0xFFFFu);
+        ls.has = true;
+        ls.top = ls.bot = 0;
+    }
+    __syncwarp();
+    if (lane == 0) {
+        Q.chead = base + n;
+        Q.progress += 1;
+        cta_unlock(&Q.lock);
+    }
+    __syncwarp();
+    return n;
+}
+
 // Walk the wide subtree of the label in queue slot `qs` (NW words, > 32
 // members) depth first over the block's shared rows; pending children on
 // the warp's stack in global memory (at most d + 1 frames of NW + 1 words).
 // The caller holds the queue lock: the slot is copied out, then released.
 // The current label lives in registers S[w] (word loops are unrolled) and in
 // the warp's wS copy (reads of word j by loop index).
-template <int NW, bool SHIST>
-__device__ __forceinline__ void cta_dfs(CtaQueue<NW> &Q, LaneWork &L, unsigned long long *shist, const CountArgs &A,
+template <int NW>
+__device__ __forceinline__ void cta_dfs(CtaQueue<NW> &Q, LaneWork &L, unsigned *sh32, const CountArgs &A,
                                         int lane, int wid, LaneState &ls, LaneCounters &lc, WalkCounters &wc,
                                         const uint32_t *adj, uint32_t *gstk, int qs, int d)
 {
@@ -190,7 +305,7 @@ __device__ __forceinline__ void cta_dfs(CtaQueue<NW> &Q, LaneWork &L, unsigned l
         __syncwarp();
         bool closed = true;
         if (s <= 32) {
-            lane_add<NW, SHIST>(L, shist, A, lane, ls, lc, adj, wS, s, h, p);
+            cta_push_small<NW>(Q, L, sh32, A, lane, wid, ls, lc, adj, s, h, p);
         } else {
             wc.nodes++;
             ++clock;
@@ -212,7 +327,7 @@ __device__ __forceinline__ void cta_dfs(CtaQueue<NW> &Q, LaneWork &L, unsigned l
             const int piv = 1023 - (int)(best & 1023u);
             if (dsum == (uint32_t)s * (uint32_t)(s - 1)) {
                 wc.leaves++;
-                tally_leaf<SHIST>(shist, A, lane, h, p + s);
+                if (lane == 0) lane_tally(sh32, A, h, p + s);
             } else {
                 const uint32_t *prow = adj + piv * RS;
                 uint32_t R[NW];
@@ -263,7 +378,7 @@ __device__ __forceinline__ void cta_dfs(CtaQueue<NW> &Q, LaneWork &L, unsigned l
                             }
                             if (cs <= 2) {
                                 const bool adjp = cs == 2 && ((adj[a * RS + (b >> 5)] >> (b & 31)) & 1u);
-                                close_small<SHIST, false>(shist, A, lane, cs, adjp, h + 1, p, NW, wc);
+                                cta_close_small<false>(sh32, A, lane, cs, adjp, h + 1, p, NW, wc);
                                 push = false;
                             }
                         }
@@ -327,7 +442,7 @@ __device__ __forceinline__ void cta_dfs(CtaQueue<NW> &Q, LaneWork &L, unsigned l
                 }
                 if (ps <= 2) {
                     const bool adjp = ps == 2 && ((adj[a * RS + (b >> 5)] >> (b & 31)) & 1u);
-                    close_small<SHIST, true>(shist, A, lane, ps, adjp, h, p + 1, NW, wc);
+                    cta_close_small<true>(sh32, A, lane, ps, adjp, h, p + 1, NW, wc);
                 } else {
                     closed = false;
 #pragma unroll
@@ -350,17 +465,18 @@ __device__ __forceinline__ void cta_dfs(CtaQueue<NW> &Q, LaneWork &L, unsigned l
 }
 
 // The block's rows for root r (all threads): member ids, their out-list
-// starts and the prefix offsets of their lengths in `scratch`, then every
-// entry of the members' out-lists looked up among the members by binary
-// search.  Q.d receives the out-degree (0 after a range error).
+// starts and the prefix offsets of their lengths in the block's global
+// scratch (gather_words), then every entry of the members' out-lists looked
+// up among the members by binary search.  Q.d receives the out-degree (0
+// after a range error).
 template <int NW>
-__device__ void cta_gather(CtaQueue<NW> &Q, unsigned char *scratch, uint32_t *adj, const CountArgs &A, uint32_t r,
+__device__ void cta_gather(CtaQueue<NW> &Q, uint32_t *scratch, uint32_t *adj, const CountArgs &A, uint32_t r,
                            int dmax)
 {
     constexpr int RS = CtaLayout<NW>::RS;
     const int64_t rbeg = A.orow[r];
     const int d = (int)(A.orow[r + 1] - rbeg);
-    uint32_t *ids = reinterpret_cast<uint32_t *>(scratch);
+    uint32_t *ids = scratch;
     uint32_t *off = ids + dmax;                                  // d + 1 prefix offsets
     int64_t *rs = reinterpret_cast<int64_t *>(off + dmax + 2);   // 8-byte aligned: 2 dmax + 2 words before
     const int tid = threadIdx.x, nt = blockDim.x;
@@ -414,6 +530,7 @@ __device__ void cta_gather(CtaQueue<NW> &Q, unsigned char *scratch, uint32_t *ad
         off[0] = 0;
         Q.d = d;
     }
+    __threadfence_block();
     __syncthreads();
     const uint32_t T = off[d];
     for (uint32_t t = tid; t < T; t += nt) {
@@ -439,78 +556,87 @@ __device__ void cta_gather(CtaQueue<NW> &Q, unsigned char *scratch, uint32_t *ad
 
 // Persistent blocks over the roots A.roots[0..A.nroots) of one class: each
 // block takes a root, gathers it, and its warps walk the root's subtrees.
-// dmax: the largest out-degree of the class (rows and stacks are sized by it).
-template <int NW, bool SHIST>
+// dmax: the largest out-degree of the class (rows and stacks are sized by
+// it).  A.gstack: per warp a DFS stack of (dmax + 1) * (NW + 1) words, then
+// per block the gather's scratch.  The lane batches and the ring of small
+// labels carry over from one root to the next: their rows are their own.
+template <int NW>
 __global__ void __launch_bounds__(32 * CTA_MAXW, 1) k_cta(CountArgs A, int dmax)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     CtaQueue<NW> &Q = *reinterpret_cast<CtaQueue<NW> *>(smem);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, warps = blockDim.x >> 5;
     LaneWork *lw = reinterpret_cast<LaneWork *>(smem + sizeof(CtaQueue<NW>));
-    unsigned long long *shist = reinterpret_cast<unsigned long long *>(lw + warps);
-    uint32_t *adj = reinterpret_cast<uint32_t *>(shist + HIST_H * HIST_P);
+    unsigned *sh32 = reinterpret_cast<unsigned *>(lw + warps);
+    uint32_t *adj = sh32 + HIST_H * HIST_P;
     LaneWork &L = lw[wid];
-    uint32_t *gstk = A.gstack + (size_t)(blockIdx.x * warps + wid) * (size_t)(dmax + 1) * (NW + 1);
+    const size_t stack_words = (size_t)(dmax + 1) * (NW + 1);
+    uint32_t *gstk = A.gstack + (size_t)(blockIdx.x * warps + wid) * stack_words;
+    uint32_t *gscratch = A.gstack + (size_t)gridDim.x * warps * stack_words +
+                         (size_t)blockIdx.x * CtaLayout<NW>::gather_words(dmax);
     LaneState ls;
     LaneCounters lc;
     WalkCounters wc;
-    if (SHIST)
-        for (int i = threadIdx.x; i < HIST_H * HIST_P; i += blockDim.x) shist[i] = 0;
-    if (threadIdx.x == 0) Q.lock = 0;
+    for (int i = threadIdx.x; i < HIST_H * HIST_P; i += blockDim.x) sh32[i] = 0;
+    for (int i = threadIdx.x; i < CTA_CQCAP; i += blockDim.x) Q.cseq[i] = 0;
+    if (threadIdx.x == 0) {
+        Q.lock = 0;
+        Q.chead = Q.ctail = 0;
+    }
     __syncthreads();
-    for (;;) {
+    bool more = true;
+    while (more) {
         // ---- next root (one decision for the whole block)
         if (threadIdx.x == 0) {
             Q.root = (vload(A.err) & (DERR_STACK | DERR_RANGE | DERR_TIMEOUT)) ? 0xFFFFFFFFu : atomicAdd(A.qhead, 1u);
-            Q.head = Q.tail = Q.busy = 0;
+            Q.head = Q.tail = 0;
+            Q.busy = 0;
             Q.progress = 0;
         }
         __syncthreads();
         const unsigned qi = Q.root;
-        if (qi >= A.nroots) break;
-        // the gather's scratch lies over the lane batches of the first warps:
-        // every lane batch is finished first
-        lane_run<SHIST>(L, shist, A, lane, ls, lc, 0xFFFFFFFFu, 0);
-        __syncthreads();
-        cta_gather<NW>(Q, reinterpret_cast<unsigned char *>(lw), adj, A, A.roots[qi], dmax);
-        const int d = Q.d;
-        if (threadIdx.x == 0 && d > 0) {
+        int d = 0;
+        if (qi < A.nroots) {
+            cta_gather<NW>(Q, gscratch, adj, A, A.roots[qi], dmax);
+            d = Q.d;
+            if (threadIdx.x == 0 && d > 0) {
 #pragma unroll
-            for (int w = 0; w < NW; ++w) {
-                const int bits = d - 32 * w;
-                Q.S[0][w] = bits >= 32 ? FULL : (bits <= 0 ? 0u : ((1u << bits) - 1u));
+                for (int w = 0; w < NW; ++w) {
+                    const int bits = d - 32 * w;
+                    Q.S[0][w] = bits >= 32 ? FULL : (bits <= 0 ? 0u : ((1u << bits) - 1u));
+                }
+                Q.hp[0] = 1u << 16;  // h = 1 (the root's hold link), p = 0
+                Q.tail = 1;
             }
-            Q.hp[0] = 1u << 16;  // h = 1 (the root's hold link), p = 0
-            Q.tail = 1;
+            __syncthreads();
+        } else {
+            more = false;  // no root left: finish the ring and the lane batches
         }
-        __syncthreads();
-        // ---- walk the root: take pending subtrees until none is left and no
-        // warp can make more
+        // ---- walk: wide subtrees of the root first, small labels of the
+        // ring into free lanes, then the warp's own lanes; the root is done
+        // when no wide subtree is pending or walked (the ring and the lanes
+        // carry over); the last round ends when the ring is empty too
         unsigned last = 0xFFFFFFFFu;
         unsigned long long t0 = global_ns();
         for (;;) {
             int took = 0;
-            if (lane == 0) {
-                if (*(volatile int *)&Q.tail > *(volatile int *)&Q.head) {
-                    if (cta_lock(&Q.lock, A.err)) {
-                        if (Q.tail > Q.head) {
-                            took = 1 + (Q.head % CTA_QCAP);
-                            Q.head += 1;
-                            Q.busy += 1;  // lock released by cta_dfs once the slot is copied
-                        } else {
-                            cta_unlock(&Q.lock);
-                        }
+            if (lane == 0 && more && *(volatile int *)&Q.tail > *(volatile int *)&Q.head) {
+                if (cta_lock(&Q.lock, A.err)) {
+                    if (Q.tail > Q.head) {
+                        took = 1 + (Q.head % CTA_QCAP);
+                        Q.head += 1;
+                        atomicAdd(&Q.busy, 1);  // the lock is released by cta_dfs once the slot is copied
                     } else {
-                        took = -1;  // timed out (status set)
+                        cta_unlock(&Q.lock);
                     }
-                } else if (*(volatile int *)&Q.busy == 0) {
-                    took = -1;  // the root is done
+                } else {
+                    took = -1;  // timed out (status set)
                 }
             }
             took = __shfl_sync(FULL, took, 0);
             if (took < 0) break;
             if (took > 0) {
-                cta_dfs<NW, SHIST>(Q, L, shist, A, lane, wid, ls, lc, wc, adj, gstk, took - 1, d);
+                cta_dfs<NW>(Q, L, sh32, A, lane, wid, ls, lc, wc, adj, gstk, took - 1, d);
                 wc.fold();
                 __syncwarp();
                 if (lane == 0) {
@@ -520,35 +646,39 @@ __global__ void __launch_bounds__(32 * CTA_MAXW, 1) k_cta(CountArgs A, int dmax)
                 t0 = global_ns();
                 continue;
             }
-            // nothing to take yet: run the lane batch a little, then look again
-            if (__ballot_sync(FULL, ls.free_()) != FULL) {
-                lane_run<SHIST>(L, shist, A, lane, ls, lc, CTA_LANE_SLICE, 0);
+            if (cta_take_small<NW>(Q, L, lane, ls, A.err) > 0) {
                 t0 = global_ns();
-            } else {
-                const unsigned pr = *(volatile unsigned *)&Q.progress;
-                if (pr != last) {
-                    last = pr;
-                    t0 = global_ns();
-                } else if (global_ns() - t0 > A.idle_ns) {
-                    if (lane == 0) atomicOr(A.err, DERR_TIMEOUT);
-                    break;
-                }
-                __nanosleep(128);
+                continue;
             }
+            if (__ballot_sync(FULL, ls.free_()) != FULL) {
+                lane_run(L, sh32, A, lane, ls, lc, CTA_LANE_SLICE, 0);
+                t0 = global_ns();
+                continue;
+            }
+            // this warp is idle: is the round over?
+            int over = 0;
+            if (lane == 0) {
+                const bool wide_done = *(volatile int *)&Q.tail == *(volatile int *)&Q.head &&
+                                       *(volatile int *)&Q.busy == 0;
+                over = more ? wide_done
+                            : wide_done && *(volatile int *)&Q.ctail == *(volatile int *)&Q.chead;
+            }
+            if (__shfl_sync(FULL, over, 0)) break;
+            const unsigned pr = *(volatile unsigned *)&Q.progress;
+            if (pr != last) {
+                last = pr;
+                t0 = global_ns();
+            } else if (global_ns() - t0 > A.idle_ns) {
+                if (lane == 0) atomicOr(A.err, DERR_TIMEOUT);
+                break;
+            }
+            __nanosleep(64);
         }
         __syncthreads();
     }
-    // ---- every root taken: finish the lane batch
-    lane_run<SHIST>(L, shist, A, lane, ls, lc, 0xFFFFFFFFu, 0);
     wc.flush(A.stats, A.cls, lane);
     lc.flush(A.stats, A.cls, lane);
-    if (SHIST) {
-        __syncthreads();
-        for (int i = threadIdx.x; i < HIST_H * HIST_P; i += blockDim.x) {
-            const unsigned long long x = shist[i];
-            if (x) atomicAdd(&A.hist[(size_t)(i / HIST_P) * A.hstride + (i % HIST_P)], x);
-        }
-    }
+    lane_hist_flush(sh32, A);
 }
 
 }  // namespace pvt

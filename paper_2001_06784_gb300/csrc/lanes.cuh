@@ -60,11 +60,36 @@ struct LaneCounters {
     }
 };
 
+// Leaf tally of one lane.  Leaves with h < HIST_H and p < HIST_P go to the
+// block's 32-bit histogram in shared memory (native 32-bit shared atomics,
+// which 32 lanes tallying at once need); an increment that wraps a counter
+// adds 2^32 to the 64-bit histogram in global memory, so the sum of the two
+// is exact at any count.  lane_hist_flush adds what is left at the end.
+__device__ __forceinline__ void lane_tally(unsigned *sh32, const CountArgs &A, int h, int p)
+{
+    if (h < HIST_H && p < HIST_P) {
+        const unsigned old = atomicAdd(&sh32[h * HIST_P + p], 1u);
+        if (old == 0xFFFFFFFFu) atomicAdd(&A.hist[(size_t)h * A.hstride + p], 1ull << 32);
+    } else {
+        atomicAdd(&A.hist[(size_t)h * A.hstride + p], 1ull);
+    }
+}
+
+// The block's 32-bit histogram into the global one (all threads of the block,
+// after the last tally).
+__device__ __forceinline__ void lane_hist_flush(unsigned *sh32, const CountArgs &A)
+{
+    __syncthreads();
+    for (int i = threadIdx.x; i < HIST_H * HIST_P; i += blockDim.x) {
+        const unsigned x = sh32[i];
+        if (x) atomicAdd(&A.hist[(size_t)(i / HIST_P) * A.hstride + (i % HIST_P)], (unsigned long long)x);
+    }
+}
+
 // Subtree of a label of at most two members in closed form, by one lane
 // (the cases of close_small in walk.cuh).
-template <bool SHIST>
-__device__ __forceinline__ void lane_close_small(unsigned long long *shist, const CountArgs &A, int cs,
-                                                 bool adjacent, int h, int p, LaneCounters &lc)
+__device__ __forceinline__ void lane_close_small(unsigned *sh32, const CountArgs &A, int cs, bool adjacent, int h,
+                                                 int p, LaneCounters &lc)
 {
     const bool split = cs == 2 && !adjacent;
     const bool hold = split && h + 1 <= A.kmax;
@@ -72,18 +97,17 @@ __device__ __forceinline__ void lane_close_small(unsigned long long *shist, cons
     lc.leaves += 1 + hold;
     lc.words += (unsigned)cs;
     if (!split) {
-        tally_lane<SHIST>(shist, A, h, p + cs);
+        lane_tally(sh32, A, h, p + cs);
         return;
     }
-    tally_lane<SHIST>(shist, A, h, p + 1);  // the pivot leaf below the pair
-    if (hold) tally_lane<SHIST>(shist, A, h + 1, p);
+    lane_tally(sh32, A, h, p + 1);  // the pivot leaf below the pair
+    if (hold) lane_tally(sh32, A, h + 1, p);
 }
 
 // One node of the lane's current subtree: label S reached with (h, p).
 // Leaves and closed forms clear `has`; otherwise hold children of three or
 // more members are pushed and the lane moves to the pivot child.
-template <bool SHIST>
-__device__ __forceinline__ void lane_node(LaneWork &L, unsigned long long *shist, const CountArgs &A, int lane,
+__device__ __forceinline__ void lane_node(LaneWork &L, unsigned *sh32, const CountArgs &A, int lane,
                                           uint32_t &S, int &h, int &p, bool &has, unsigned &top, unsigned bot,
                                           LaneCounters &lc)
 {
@@ -91,7 +115,7 @@ __device__ __forceinline__ void lane_node(LaneWork &L, unsigned long long *shist
     ++lc.nodes;
     if (s == 0) {
         ++lc.leaves;
-        tally_lane<SHIST>(shist, A, h, p);
+        lane_tally(sh32, A, h, p);
         has = false;
         return;
     }
@@ -116,7 +140,7 @@ __device__ __forceinline__ void lane_node(LaneWork &L, unsigned long long *shist
     lc.words += (unsigned)s;
     if (dsum == (uint32_t)s * (uint32_t)(s - 1)) {
         ++lc.leaves;
-        tally_lane<SHIST>(shist, A, h, p + s);
+        lane_tally(sh32, A, h, p + s);
         has = false;
         return;
     }
@@ -133,7 +157,7 @@ __device__ __forceinline__ void lane_node(LaneWork &L, unsigned long long *shist
             const int cs = __popc(child);
             if (cs <= 2) {
                 const bool adj = cs == 2 && ((L.rows[__ffs(child) - 1][lane] >> (31 - __clz(child))) & 1u);
-                lane_close_small<SHIST>(shist, A, cs, adj, h + 1, p, lc);
+                lane_close_small(sh32, A, cs, adj, h + 1, p, lc);
             } else {
                 L.stkS[top & (LSTK - 1)][lane] = child;
                 L.stkHP[top & (LSTK - 1)][lane] = ((uint32_t)(h + 1) << 16) | (uint32_t)p;
@@ -147,7 +171,7 @@ __device__ __forceinline__ void lane_node(LaneWork &L, unsigned long long *shist
     const int ps = __popc(P);
     if (ps <= 2) {
         const bool adj = ps == 2 && ((L.rows[__ffs(P) - 1][lane] >> (31 - __clz(P))) & 1u);
-        lane_close_small<SHIST>(shist, A, ps, adj, h, p + 1, lc);
+        lane_close_small(sh32, A, ps, adj, h, p + 1, lc);
         has = false;
     } else {
         S = P;
@@ -236,72 +260,92 @@ __device__ __forceinline__ void lane_gather(LaneWork &L, const CountArgs &A, int
     S = d >= 32 ? FULL : ((1u << d) - 1u);
 }
 
+// Lane j takes frame `item` of the emitted buffer: its 32 rows into column j
+// with eight 16-byte loads (every lane its own frame, so the warp's stores
+// hit 32 distinct banks), its label and (h, p).
+__device__ __forceinline__ void lane_load_frame(LaneWork &L, const uint32_t *fr, int lane, uint32_t &S, int &h,
+                                                int &p)
+{
+    const uint4 *v = reinterpret_cast<const uint4 *>(fr + 4);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        const uint4 x = __ldcs(v + q);
+        L.rows[4 * q + 0][lane] = x.x;
+        L.rows[4 * q + 1][lane] = x.y;
+        L.rows[4 * q + 2][lane] = x.z;
+        L.rows[4 * q + 3][lane] = x.w;
+    }
+    const uint4 head = __ldcs(reinterpret_cast<const uint4 *>(fr));
+    S = head.z;
+    h = (int)(head.y >> 16);
+    p = (int)(head.y & 0xFFFFu);
+}
+
+constexpr unsigned LANE_CLAIM = 32;  // source items a warp claims at once
+
 // The lane walk over one source of items: the first `nitems` emitted frames
 // (ROOTS = false: A.emit) or the roots A.roots[0..nroots) (ROOTS = true).
-// Items are claimed through qctl[Q_ROOT]; qctl[Q_OUT] counts items not yet
-// finished (a warp returns its items once every lane is idle), and warps
-// that run dry wait on the ring queue for donated frames until it drops to
-// zero (walk.cuh: queue_take).
-template <bool SHIST, bool ROOTS>
-__device__ void lane_walk(LaneWork &L, unsigned long long *shist, const CountArgs &A, int lane, unsigned nitems,
-                          int slot)
+// A warp claims LANE_CLAIM items at a time through qctl[Q_ROOT] and hands
+// them to its free lanes; qctl[Q_OUT] counts items not yet finished (a warp
+// returns its items once every lane is idle), and warps that run dry wait on
+// the ring queue for donated frames until it drops to zero (walk.cuh:
+// queue_take).
+template <bool ROOTS>
+__device__ void lane_walk(LaneWork &L, unsigned *sh32, const CountArgs &A, int lane, unsigned nitems, int slot)
 {
     LaneCounters lc;
     uint32_t S = 0;
     int h = 0, p = 0;
     bool has = false;
     unsigned top = 0, bot = 0;
-    unsigned held = 0;      // items this warp took and has not returned (uniform)
-    bool src_done = false;  // uniform
+    unsigned held = 0;           // items this warp took and has not returned (uniform)
+    unsigned cur = 0, end = 0;   // claimed, not yet started items [cur, end) (uniform)
+    bool src_done = false;       // uniform
     unsigned steps = 0;
     for (;;) {
         unsigned freeM = __ballot_sync(FULL, !has && top == bot);
-        if (freeM) {
-            if (!src_done) {
-                const unsigned nf = __popc(freeM);
-                unsigned base = 0;
-                if (lane == 0) base = vload(A.qctl + Q_ROOT) < nitems ? atomicAdd(A.qctl + Q_ROOT, nf) : nitems;
+        if (freeM && !src_done) {
+            if (cur == end) {
+                unsigned base = nitems;
+                if (lane == 0 && vload(A.qctl + Q_ROOT) < nitems) base = atomicAdd(A.qctl + Q_ROOT, LANE_CLAIM);
                 base = __shfl_sync(FULL, base, 0);
-                const unsigned got = base >= nitems ? 0u : min(nf, nitems - base);
-                if (got < nf) src_done = true;
-                if (got) {
-                    // the first `got` free lanes take items base .. base+got-1
-                    const bool mine = ((freeM >> lane) & 1u) && (unsigned)__popc(freeM & ((1u << lane) - 1u)) < got;
-                    const unsigned item = base + (unsigned)__popc(freeM & ((1u << lane) - 1u));
-                    if (ROOTS) {
-                        if (mine) {
-                            lane_gather(L, A, lane, A.roots[item], S, A.err);
-                            h = 1;
-                            p = 0;
-                            has = true;
-                        }
-                    } else {
-                        unsigned m = freeM;
-#pragma unroll 4
-                        for (unsigned i = 0; i < got; ++i) {
-                            const int j = __ffs(m) - 1;
-                            m &= m - 1;
-                            const uint32_t *fr = A.emit + (size_t)(base + i) * FRAME_WORDS;
-                            L.rows[lane][j] = __ldcs(fr + 4 + lane);
-                        }
-                        if (mine) {
-                            const uint32_t *fr = A.emit + (size_t)item * FRAME_WORDS;
-                            const uint32_t hp = __ldcs(fr + 1);
-                            S = __ldcs(fr + 2);
-                            h = (int)(hp >> 16);
-                            p = (int)(hp & 0xFFFFu);
-                            has = true;
-                        }
+                if (base >= nitems) {
+                    src_done = true;
+                } else {
+                    cur = base;
+                    end = min(base + LANE_CLAIM, nitems);
+                    if (!ROOTS && lane < (int)(end - cur)) {
+                        // the claimed frames into L2 ahead of their lanes
+                        const char *a = reinterpret_cast<const char *>(A.emit + (size_t)(cur + lane) * FRAME_WORDS);
+                        asm volatile("prefetch.global.L2 [%0];" ::"l"(a));
+                        asm volatile("prefetch.global.L2 [%0];" ::"l"(a + 128));
                     }
-                    held += got;
-                    __syncwarp();
                 }
+            }
+            if (cur < end) {
+                // the first free lanes take items cur, cur+1, ...
+                const unsigned got = min((unsigned)__popc(freeM), end - cur);
+                const unsigned rank = (unsigned)__popc(freeM & ((1u << lane) - 1u));
+                if (((freeM >> lane) & 1u) && rank < got) {
+                    const unsigned item = cur + rank;
+                    if (ROOTS) {
+                        lane_gather(L, A, lane, A.roots[item], S, A.err);
+                        h = 1;
+                        p = 0;
+                    } else {
+                        lane_load_frame(L, A.emit + (size_t)item * FRAME_WORDS, lane, S, h, p);
+                    }
+                    has = true;
+                }
+                cur += got;
+                held += got;
+                __syncwarp();
                 freeM = __ballot_sync(FULL, !has && top == bot);
             }
-            if (freeM && src_done) {
-                lane_steal(L, lane, freeM, S, h, p, has, top, bot);
-                freeM = __ballot_sync(FULL, !has && top == bot);
-            }
+        }
+        if (freeM && src_done) {
+            lane_steal(L, lane, freeM, S, h, p, has, top, bot);
+            freeM = __ballot_sync(FULL, !has && top == bot);
             if (freeM == FULL) {
                 // every lane idle: return this warp's items, then wait for a
                 // donated frame (or the end of the launch)
@@ -313,19 +357,14 @@ __device__ void lane_walk(LaneWork &L, unsigned long long *shist, const CountArg
                 v = __shfl_sync(FULL, v, 0);
                 if (kind != 1) break;
                 const uint32_t *fr = A.qframes + (size_t)(v & (A.qcap - 1u)) * FRAME_WORDS;
-                L.rows[lane][0] = __ldcg(fr + 4 + lane);
-                uint32_t hp = 0, s0 = 0;
                 if (lane == 0) {
-                    hp = __ldcg(fr + 1);
-                    s0 = __ldcg(fr + 2);
-                }
-                __syncwarp();
-                if (lane == 0) {
-                    __threadfence();
-                    atomicExch(A.qdone + (v & (A.qcap - 1u)), v + 1u);
-                    S = s0;
+                    const uint32_t hp = __ldcg(fr + 1);
+                    S = __ldcg(fr + 2);
                     h = (int)(hp >> 16);
                     p = (int)(hp & 0xFFFFu);
+                    for (int v2 = 0; v2 < 32; ++v2) L.rows[v2][0] = __ldcg(fr + 4 + v2);
+                    __threadfence();
+                    atomicExch(A.qdone + (v & (A.qcap - 1u)), v + 1u);
                     has = true;
                 }
                 held = 1;
@@ -342,7 +381,7 @@ __device__ void lane_walk(LaneWork &L, unsigned long long *shist, const CountArg
             p = (int)(hp & 0xFFFFu);
             has = true;
         }
-        if (has) lane_node<SHIST>(L, shist, A, lane, S, h, p, has, top, bot, lc);
+        if (has) lane_node(L, sh32, A, lane, S, h, p, has, top, bot, lc);
         __syncwarp();
         if (++steps % LANE_DONATE_EVERY == 0) {
             // a warp waits on the ring: donate the oldest pending entry of the
@@ -376,21 +415,17 @@ __device__ void lane_walk(LaneWork &L, unsigned long long *shist, const CountArg
     lc.flush(A.stats, slot, lane);
 }
 
-template <bool SHIST>
-constexpr size_t lane_smem_bytes()
-{
-    return sizeof(LaneWork) * LANE_WPB + (SHIST ? sizeof(unsigned long long) * HIST_H * HIST_P : 0);
-}
+constexpr size_t lane_smem_bytes() { return sizeof(LaneWork) * LANE_WPB + sizeof(unsigned) * HIST_H * HIST_P; }
 
 // ROOTS = false: every emitted compacted frame (A.emit, the count in
 // *A.emit_count capped at A.emit_cap), walk statistics to slot FRAMES_SLOT;
 // ROOTS = true: the roots A.roots[0..A.nroots) of the <= 32 class, slot A.cls.
-template <bool SHIST, bool ROOTS>
+template <bool ROOTS>
 __global__ void __launch_bounds__(32 * LANE_WPB, 2) k_lanes(CountArgs A)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     LaneWork *lw = reinterpret_cast<LaneWork *>(smem);
-    unsigned long long *shist = reinterpret_cast<unsigned long long *>(lw + LANE_WPB);
+    unsigned *sh32 = reinterpret_cast<unsigned *>(lw + LANE_WPB);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     unsigned nitems = A.nroots;
     if (!ROOTS) {
@@ -398,18 +433,10 @@ __global__ void __launch_bounds__(32 * LANE_WPB, 2) k_lanes(CountArgs A)
         nitems = (unsigned)min(emitted, (unsigned long long)A.emit_cap);
         if (blockIdx.x == 0 && threadIdx.x == 0) A.stats[3 + NCLASS + 1] = emitted;
     }
-    if (SHIST) {
-        for (int i = threadIdx.x; i < HIST_H * HIST_P; i += blockDim.x) shist[i] = 0;
-        __syncthreads();
-    }
-    lane_walk<SHIST, ROOTS>(lw[wid], shist, A, lane, nitems, ROOTS ? A.cls : NCLASS);
-    if (SHIST) {
-        __syncthreads();
-        for (int i = threadIdx.x; i < HIST_H * HIST_P; i += blockDim.x) {
-            const unsigned long long x = shist[i];
-            if (x) atomicAdd(&A.hist[(size_t)(i / HIST_P) * A.hstride + (i % HIST_P)], x);
-        }
-    }
+    for (int i = threadIdx.x; i < HIST_H * HIST_P; i += blockDim.x) sh32[i] = 0;
+    __syncthreads();
+    lane_walk<ROOTS>(lw[wid], sh32, A, lane, nitems, ROOTS ? A.cls : NCLASS);
+    lane_hist_flush(sh32, A);
 }
 
 }  // namespace pvt

@@ -81,7 +81,7 @@ struct pvt_dag {
     unsigned long long *h_stats = nullptr;  // pinned host copy
     pvt_stats stats = {};
     bool profiling = false;
-    pvt_policy policy = {1, 4, {0, 0, 1, 1, 1, 1, 1}, 0, 1, 0, 1, {0, 0, 0, 0, 0, 1, 1}};
+    pvt_policy policy = {1, 4, {0, 0, 1, 1, 1, 1, 1}, 0, 1, 0, 1, {0, 0, 0, 0, 0, 1, 1}, 0};
     pvt::DevBuf<uint32_t> cframes;  // compacted frames emitted by the wide walks
     bool serial = false;           // launch the classes one after another on the caller's stream
     bool capturing = false;        // recording a CUDA graph: no phase events

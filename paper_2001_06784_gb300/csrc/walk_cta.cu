@@ -9,13 +9,13 @@ template <int NW>
 static pvt_status launch_cta_nw(pvt_dag *g, CountArgs A, int cls, int dmax, cudaStream_t s)
 {
     using Lay = CtaLayout<NW>;
-    auto kern = k_cta<NW, true>;
+    auto kern = k_cta<NW>;
     int optin = 0;
     PVT_CK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, g->device));
     const size_t fixed = Lay::bytes(0, dmax);
     int warps = fixed < (size_t)optin ? (int)(((size_t)optin - fixed) / sizeof(LaneWork)) : 0;
     warps = std::min(warps, CTA_MAXW);
-    if (warps < 2 || Lay::gather_bytes(dmax) > (size_t)warps * sizeof(LaneWork)) {
+    if (warps < 1) {
         set_error("CTA walk: shared memory too small for out-degree " + std::to_string(dmax));
         return PVT_EINVAL;
     }
@@ -28,7 +28,8 @@ static pvt_status launch_cta_nw(pvt_dag *g, CountArgs A, int cls, int dmax, cuda
         return PVT_ECUDA;
     }
     const unsigned blocks = std::max(1u, std::min<unsigned>((unsigned)(g->num_sms * per_sm), A.nroots));
-    pvt_status st = grow(g->gstack[cls], (size_t)blocks * warps * (dmax + 1) * (NW + 1), s);
+    pvt_status st =
+        grow(g->gstack[cls], (size_t)blocks * warps * (dmax + 1) * (NW + 1) + (size_t)blocks * Lay::gather_words(dmax), s);
     if (st != PVT_OK) return st;
     A.gstack = g->gstack[cls].p;
     phase_begin(g, 1 + cls, s);

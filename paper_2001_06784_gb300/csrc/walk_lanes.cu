@@ -7,8 +7,8 @@ namespace pvt {
 template <bool ROOTS>
 static pvt_status launch_lanes_kernel(pvt_dag *g, const CountArgs &A, int phase, cudaStream_t s)
 {
-    constexpr size_t smem = lane_smem_bytes<true>();
-    auto kern = k_lanes<true, ROOTS>;
+    constexpr size_t smem = lane_smem_bytes();
+    auto kern = k_lanes<ROOTS>;
     PVT_CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
     PVT_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * LANE_WPB, smem));
