@@ -655,23 +655,27 @@ __global__ void __launch_bounds__(32 * CTA_MAXW, 1) k_cta(CountArgs A, int dmax)
                 t0 = global_ns();
                 continue;
             }
-            // this warp is idle: is the round over?
-            int over = 0;
+            // this warp is idle: is the round over, or has the wait run out?
+            // Lane 0 decides for the warp (every lane must leave the loop
+            // together: the block barrier below waits for all of them)
+            int act = 0;  // 1: the round is over, 2: the wait gave up
             if (lane == 0) {
                 const bool wide_done = *(volatile int *)&Q.tail == *(volatile int *)&Q.head &&
                                        *(volatile int *)&Q.busy == 0;
-                over = more ? wide_done
-                            : wide_done && *(volatile int *)&Q.ctail == *(volatile int *)&Q.chead;
+                if (more ? wide_done : wide_done && *(volatile int *)&Q.ctail == *(volatile int *)&Q.chead) {
+                    act = 1;
+                } else {
+                    const unsigned pr = *(volatile unsigned *)&Q.progress;
+                    if (pr != last) {
+                        last = pr;
+                        t0 = global_ns();
+                    } else if (global_ns() - t0 > A.idle_ns) {
+                        atomicOr(A.err, DERR_TIMEOUT);
+                        act = 2;
+                    }
+                }
             }
-            if (__shfl_sync(FULL, over, 0)) break;
-            const unsigned pr = *(volatile unsigned *)&Q.progress;
-            if (pr != last) {
-                last = pr;
-                t0 = global_ns();
-            } else if (global_ns() - t0 > A.idle_ns) {
-                if (lane == 0) atomicOr(A.err, DERR_TIMEOUT);
-                break;
-            }
+            if (__shfl_sync(FULL, act, 0)) break;
             __nanosleep(64);
         }
         __syncthreads();
