@@ -287,11 +287,11 @@ pvt_status pvt_measure_popc_rate(double *pairs_per_s, void *stream);
  *               instead.  A wait that gives up ends the call with
  *               PVT_ETIMEOUT and leaves the library usable; the field
  *               exists to exercise that path (0 .. 10^9).
- *   lanes       1 (default): in global counts of the persistent form, labels
- *               of at most 32 members -- the roots of the <= 32 class and the
- *               frames of the two-phase walk -- are walked one subtree per
- *               lane, 32 subtrees per warp, instead of one per warp; 0: one
- *               per warp.  The walked tree is the same either way.
+ *   lanes       1 (default): in global counts of the persistent form, the
+ *               frames of the two-phase walk (labels of at most 32 members)
+ *               are walked one subtree per lane, 32 subtrees per warp,
+ *               instead of one per warp; 0: one per warp.  The walked tree
+ *               is the same either way.
  *   cta[c]      per out-degree class c: 1 walks each root of the class with a
  *               whole thread block over one shared copy of its adjacency
  *               rows, the block's warps sharing its subtrees and walking its

@@ -273,11 +273,7 @@ static pvt_status launch_all(pvt_dag *g, const CountArgs &A0, cudaStream_t s)
         cudaStream_t cs = serial ? s : g->side[c];
         if (!serial) PVT_CK(cudaStreamWaitEvent(cs, g->ev_fork, 0));
         switch (c) {
-            case 1:
-                st = MODE == MODE_GLOBAL && g->policy.lanes && g->policy.persistent
-                         ? launch_lanes_roots(g, A0, c, cs)
-                         : launch_class<1, MODE, MODE == MODE_GLOBAL>(g, A0, c, cs);
-                break;
+            case 1: st = launch_class<1, MODE, MODE == MODE_GLOBAL>(g, A0, c, cs); break;
             case 2: st = launch_class<2, MODE, MODE == MODE_GLOBAL>(g, A, c, cs); break;
             case 4:
             case 5:

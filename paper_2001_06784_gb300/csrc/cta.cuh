@@ -103,7 +103,7 @@ __device__ __forceinline__ void cta_close_small(unsigned *sh32, const CountArgs 
 
 // Run the warp's lane batch: at most `budget` node steps, stopping early
 // once `stop_free` lanes are free (0: only when every lane is idle).
-__device__ void lane_run(LaneWork &L, unsigned *sh32, const CountArgs &A, int lane, LaneState &ls,
+__device__ inline void lane_run(LaneWork &L, unsigned *sh32, const CountArgs &A, int lane, LaneState &ls,
                          LaneCounters &lc, unsigned budget, int stop_free)
 {
     for (unsigned step = 0; step < budget; ++step) {

@@ -1,8 +1,8 @@
 // One-word SCT walk with one subtree per lane (global counts).
 //
-// Labels of at most 32 members -- every root of the <= 32 out-degree class,
-// and the compacted subtrees that the wide walks emit as frames -- hold
-// almost all nodes of the SCT, and each of their nodes is a handful of
+// Labels of at most 32 members -- the compacted subtrees that the wide
+// walks emit as frames, and the small labels below a dense root (cta.cuh) --
+// hold almost all nodes of the SCT, and each of their nodes is a handful of
 // word operations: pivot selection is |S| ANDs and population counts on
 // one-word rows (Alg. 1 pivot step), each child one AND (Alg. 1 hold step).
 // A warp that walks one such subtree spends tens of instructions of
@@ -17,8 +17,8 @@
 // closed forms of walk.cuh) -- so the tree, its statistics and the (h, p)
 // leaf histogram are exactly those of the warp walk.
 //
-// Work moves at three levels: a free lane takes the next item of the
-// launch's source (a frame, or a root whose adjacency it gathers itself); a
+// Work moves at three levels: a free lane takes the next frame of the
+// launch's source; a
 // free lane with the source exhausted takes the oldest pending stack entry
 // of a busy lane of its warp (with that lane's rows); and, through the ring
 // queue of walk.cuh, a busy warp donates the oldest pending entry of its
@@ -217,49 +217,6 @@ __device__ __forceinline__ unsigned lane_steal(LaneWork &L, int lane, unsigned f
     return __ballot_sync(FULL, recv);
 }
 
-// Gather root r's induced adjacency into the lane's rows (lane-private: no
-// atomics).  Members 0..d-1 are N+(r) in ascending id; their ids sit in the
-// lane's (empty) stack column while it scans each member's out-list and
-// looks every entry up among them by binary search.  d <= 32.
-__device__ __forceinline__ void lane_gather(LaneWork &L, const CountArgs &A, int lane, uint32_t r, uint32_t &S,
-                                            unsigned *err)
-{
-    const int64_t rbeg = A.orow[r];
-    const int d = (int)(A.orow[r + 1] - rbeg);
-    if (d > 32 || d < 0) {
-        atomicOr(err, DERR_RANGE);
-        S = 0;
-        return;
-    }
-    for (int i = 0; i < d; ++i) {
-        L.stkS[i][lane] = A.ocol[rbeg + i];
-        L.rows[i][lane] = 0;
-    }
-    for (int i = 0; i < d; ++i) {
-        const uint32_t id = L.stkS[i][lane];
-        const int64_t b = A.orow[id], e = A.orow[id + 1];
-        for (int64_t t = b; t < e; t += 4) {
-            uint32_t xv[4];
-#pragma unroll
-            for (int q = 0; q < 4; ++q) xv[q] = t + q < e ? A.ocol[t + q] : 0xFFFFFFFFu;
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                if (t + q >= e) break;
-                int lo = 0, hi = d;
-                while (lo < hi) {
-                    const int mid = (lo + hi) >> 1;
-                    if (L.stkS[mid][lane] < xv[q]) lo = mid + 1; else hi = mid;
-                }
-                if (lo < d && L.stkS[lo][lane] == xv[q]) {
-                    L.rows[i][lane] |= 1u << lo;
-                    L.rows[lo][lane] |= 1u << i;
-                }
-            }
-        }
-    }
-    S = d >= 32 ? FULL : ((1u << d) - 1u);
-}
-
 // Lane j takes frame `item` of the emitted buffer: its 32 rows into column j
 // with eight 16-byte loads (every lane its own frame, so the warp's stores
 // hit 32 distinct banks), its label and (h, p).
@@ -283,15 +240,13 @@ __device__ __forceinline__ void lane_load_frame(LaneWork &L, const uint32_t *fr,
 
 constexpr unsigned LANE_CLAIM = 32;  // source items a warp claims at once
 
-// The lane walk over one source of items: the first `nitems` emitted frames
-// (ROOTS = false: A.emit) or the roots A.roots[0..nroots) (ROOTS = true).
-// A warp claims LANE_CLAIM items at a time through qctl[Q_ROOT] and hands
-// them to its free lanes; qctl[Q_OUT] counts items not yet finished (a warp
+// The lane walk over the first `nitems` emitted frames (A.emit).  A warp
+// claims LANE_CLAIM frames at a time through qctl[Q_ROOT] and hands them to
+// its free lanes; qctl[Q_OUT] counts items not yet finished (a warp
 // returns its items once every lane is idle), and warps that run dry wait on
 // the ring queue for donated frames until it drops to zero (walk.cuh:
 // queue_take).
-template <bool ROOTS>
-__device__ void lane_walk(LaneWork &L, unsigned *sh32, const CountArgs &A, int lane, unsigned nitems, int slot)
+__device__ inline void lane_walk(LaneWork &L, unsigned *sh32, const CountArgs &A, int lane, unsigned nitems, int slot)
 {
     LaneCounters lc;
     uint32_t S = 0;
@@ -314,7 +269,7 @@ __device__ void lane_walk(LaneWork &L, unsigned *sh32, const CountArgs &A, int l
                 } else {
                     cur = base;
                     end = min(base + LANE_CLAIM, nitems);
-                    if (!ROOTS && lane < (int)(end - cur)) {
+                    if (lane < (int)(end - cur)) {
                         // the claimed frames into L2 ahead of their lanes
                         const char *a = reinterpret_cast<const char *>(A.emit + (size_t)(cur + lane) * FRAME_WORDS);
                         asm volatile("prefetch.global.L2 [%0];" ::"l"(a));
@@ -327,14 +282,7 @@ __device__ void lane_walk(LaneWork &L, unsigned *sh32, const CountArgs &A, int l
                 const unsigned got = min((unsigned)__popc(freeM), end - cur);
                 const unsigned rank = (unsigned)__popc(freeM & ((1u << lane) - 1u));
                 if (((freeM >> lane) & 1u) && rank < got) {
-                    const unsigned item = cur + rank;
-                    if (ROOTS) {
-                        lane_gather(L, A, lane, A.roots[item], S, A.err);
-                        h = 1;
-                        p = 0;
-                    } else {
-                        lane_load_frame(L, A.emit + (size_t)item * FRAME_WORDS, lane, S, h, p);
-                    }
+                    lane_load_frame(L, A.emit + (size_t)(cur + rank) * FRAME_WORDS, lane, S, h, p);
                     has = true;
                 }
                 cur += got;
@@ -416,27 +364,5 @@ __device__ void lane_walk(LaneWork &L, unsigned *sh32, const CountArgs &A, int l
 }
 
 constexpr size_t lane_smem_bytes() { return sizeof(LaneWork) * LANE_WPB + sizeof(unsigned) * HIST_H * HIST_P; }
-
-// ROOTS = false: every emitted compacted frame (A.emit, the count in
-// *A.emit_count capped at A.emit_cap), walk statistics to slot FRAMES_SLOT;
-// ROOTS = true: the roots A.roots[0..A.nroots) of the <= 32 class, slot A.cls.
-template <bool ROOTS>
-__global__ void __launch_bounds__(32 * LANE_WPB, 2) k_lanes(CountArgs A)
-{
-    extern __shared__ __align__(16) unsigned char smem[];
-    LaneWork *lw = reinterpret_cast<LaneWork *>(smem);
-    unsigned *sh32 = reinterpret_cast<unsigned *>(lw + LANE_WPB);
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    unsigned nitems = A.nroots;
-    if (!ROOTS) {
-        const unsigned long long emitted = *(volatile unsigned long long *)A.emit_count;
-        nitems = (unsigned)min(emitted, (unsigned long long)A.emit_cap);
-        if (blockIdx.x == 0 && threadIdx.x == 0) A.stats[3 + NCLASS + 1] = emitted;
-    }
-    for (int i = threadIdx.x; i < HIST_H * HIST_P; i += blockDim.x) sh32[i] = 0;
-    __syncthreads();
-    lane_walk<ROOTS>(lw[wid], sh32, A, lane, nitems, ROOTS ? A.cls : NCLASS);
-    lane_hist_flush(sh32, A);
-}
 
 }  // namespace pvt

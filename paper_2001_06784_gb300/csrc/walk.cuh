@@ -1100,9 +1100,8 @@ static __global__ void k_split_init(uint32_t *qctl, unsigned nroots)
 
 constexpr unsigned SPLIT_QCAP = 1u << 17;
 
-// The lane walk of one-word labels (lanes.cuh, walk_lanes.cu): the roots of
-// out-degree class cls (<= 32), and the frames of the two-phase count.
-pvt_status launch_lanes_roots(pvt_dag *g, const CountArgs &base, int cls, cudaStream_t s);
+// The lane walk of one-word labels (lanes.cuh, walk_lanes.cu): the frames of
+// the two-phase count.
 pvt_status launch_lanes_frames(pvt_dag *g, const CountArgs &base, cudaStream_t s);
 // The CTA-per-root walk (cta.cuh, walk_cta.cu) of out-degree class cls >= 4.
 pvt_status launch_cta_class(pvt_dag *g, const CountArgs &base, int cls, cudaStream_t s);

@@ -1,14 +1,31 @@
-// Launchers of the lane walk (lanes.cuh): the roots of the <= 32 out-degree
-// class and the compacted frames of the two-phase global count.
+// Launcher of the lane walk (lanes.cuh) over the compacted frames of the
+// two-phase global count.
 #include "lanes.cuh"
 
 namespace pvt {
 
-template <bool ROOTS>
+// Every emitted compacted frame (A.emit, the count in *A.emit_count capped
+// at A.emit_cap); walk statistics to slot FRAMES_SLOT.
+__global__ void __launch_bounds__(32 * LANE_WPB, 2) k_lanes(CountArgs A)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    LaneWork *lw = reinterpret_cast<LaneWork *>(smem);
+    unsigned *sh32 = reinterpret_cast<unsigned *>(lw + LANE_WPB);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const unsigned long long emitted = *(volatile unsigned long long *)A.emit_count;
+    const unsigned nitems = (unsigned)min(emitted, (unsigned long long)A.emit_cap);
+    if (blockIdx.x == 0 && threadIdx.x == 0) A.stats[3 + NCLASS + 1] = emitted;
+    for (int i = threadIdx.x; i < HIST_H * HIST_P; i += blockDim.x) sh32[i] = 0;
+    __syncthreads();
+    lane_walk(lw[wid], sh32, A, lane, nitems, NCLASS);
+    lane_hist_flush(sh32, A);
+}
+
+
 static pvt_status launch_lanes_kernel(pvt_dag *g, const CountArgs &A, int phase, cudaStream_t s)
 {
     constexpr size_t smem = lane_smem_bytes();
-    auto kern = k_lanes<ROOTS>;
+    auto kern = k_lanes;
     PVT_CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
     PVT_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * LANE_WPB, smem));
@@ -16,19 +33,12 @@ static pvt_status launch_lanes_kernel(pvt_dag *g, const CountArgs &A, int phase,
         set_error("lane walk kernel cannot be resident (shared memory)");
         return PVT_ECUDA;
     }
-    unsigned grid = (unsigned)(g->num_sms * per_sm);
-    if (ROOTS) grid = std::max(1u, std::min<unsigned>(grid, (A.nroots + 32 * LANE_WPB - 1) / (32 * LANE_WPB)));
+    const unsigned grid = (unsigned)(g->num_sms * per_sm);
     phase_begin(g, phase, s);
     kern<<<grid, 32 * LANE_WPB, smem, s>>>(A);
     PVT_CK(cudaGetLastError());
     phase_end(g, phase, s);
     return PVT_OK;
-}
-
-// Queue counters of a lane launch: nothing claimed, `out` items outstanding.
-static __global__ void k_lanes_init(uint32_t *qctl, unsigned out)
-{
-    for (int i = threadIdx.x; i < QCTL_WORDS; i += blockDim.x) qctl[i] = i == Q_OUT ? out : 0u;
 }
 
 // Frame counters of the second phase: the emitted count is final on the device.
@@ -53,22 +63,6 @@ static pvt_status lane_ring(pvt_dag *g, CountArgs &A, int q, cudaStream_t s)
     return PVT_OK;
 }
 
-pvt_status launch_lanes_roots(pvt_dag *g, const CountArgs &base, int cls, cudaStream_t s)
-{
-    const unsigned cnt = (unsigned)g->wcnt[cls];
-    if (cnt == 0) return PVT_OK;
-    CountArgs A = base;
-    A.roots = g->wroots + g->wstart[cls];
-    A.nroots = cnt;
-    A.cls = cls;
-    pvt_status st = lane_ring(g, A, cls, s);
-    if (st != PVT_OK) return st;
-    k_lanes_init<<<1, 128, 0, s>>>(A.qctl, cnt);
-    PVT_CK(cudaGetLastError());
-    g->stats.launches += 2;
-    return launch_lanes_kernel<true>(g, A, 1 + cls, s);
-}
-
 pvt_status launch_lanes_frames(pvt_dag *g, const CountArgs &base, cudaStream_t s)
 {
     CountArgs A = base;
@@ -78,7 +72,7 @@ pvt_status launch_lanes_frames(pvt_dag *g, const CountArgs &base, cudaStream_t s
     k_lanes_frames_init<<<1, 128, 0, s>>>(A.qctl, A.emit_count, A.emit_cap);
     PVT_CK(cudaGetLastError());
     g->stats.launches += 2;
-    return launch_lanes_kernel<false>(g, A, PH_FRAMES, s);
+    return launch_lanes_kernel(g, A, PH_FRAMES, s);
 }
 
 }  // namespace pvt
