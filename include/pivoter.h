@@ -188,8 +188,10 @@ pvt_status pvt_local_distribution(const uint64_t *table, int64_t rows, int32_t K
  * figures are of the walk the device performed: nodes visited (leaves and
  * roots with no out-neighbour included; a node whose label is a nonempty
  * clique is closed as one leaf, so the |S| nodes of its pivot chain are not
- * visited), root-to-leaf paths, and the bitset words ANDed and popcounted in
- * pivot selection (|S| * ceil(d/32) per internal node).  ms[] holds device
+ * visited), root-to-leaf paths, and the pivot words: |S| * ceil(|S|/32) per
+ * internal node, the AND + population-count word pairs of pivot selection
+ * over rows restricted to the label's own members -- a property of the tree,
+ * whichever row width a kernel walks it in.  ms[] holds device
  * time per phase when profiling is on (else zeros): [0] peel, [1] orient
  * (DAG CSR and root classes), [2..7] the walk kernels of out-degree classes
  * <=32, <=64, <=128, <=256, <=512, <=1024, [8] combine/finish, [9] the

@@ -27,6 +27,17 @@ constexpr int CTA_MAXW = 16;                 // warps per block at most
 constexpr unsigned CTA_DONATE_EVERY = 2;     // wide nodes between looks at the block's queue
 constexpr unsigned CTA_LANE_SLICE = 64;      // lane steps between looks while waiting
 constexpr unsigned long long CTA_LOCK_LIMIT_NS = 2000000000ull;  // 2 s for the block's queue lock
+// Labels of 33..128 members below a wider root are relabelled to rows of
+// MID_NW words (in the warp's shared memory) and walked there: a pivot word
+// pair then costs a 4-word row instead of the root's NW words.
+constexpr int MID_NW = 4, MID_RS = 5, MID_D = 32 * MID_NW;
+
+// Per-warp shared state of the CTA walk beside its lane batch: the rows of a
+// relabelled mid-size label and the member list of a label being relabelled.
+struct alignas(16) CtaWarp {
+    uint32_t mid[MID_D * MID_RS];
+    uint16_t mem[MID_D];
+};
 
 // Shared state of a block, before the per-warp lane batches.
 template <int NW>
@@ -57,8 +68,14 @@ struct CtaLayout {
     // then the root's rows (dmax rows of RS words)
     __host__ __device__ static size_t bytes(int warps, int dmax)
     {
-        return sizeof(CtaQueue<NW>) + sizeof(LaneWork) * warps + sizeof(unsigned) * HIST_H * HIST_P +
-               (size_t)dmax * RS * sizeof(uint32_t);
+        return sizeof(CtaQueue<NW>) + (sizeof(LaneWork) + sizeof(CtaWarp)) * warps +
+               sizeof(unsigned) * HIST_H * HIST_P + (size_t)dmax * RS * sizeof(uint32_t);
+    }
+    // per warp in global memory: the DFS stack of the root's level, then
+    // that of the mid level
+    __host__ __device__ static size_t stack_words(int dmax)
+    {
+        return (size_t)(dmax + 1) * (NW + 1) + (size_t)(MID_D + 1) * (MID_NW + 1);
     }
     // global scratch of a block's gather: member ids, prefix offsets (dmax + 2
     // words) and out-list starts (dmax 8-byte words)
@@ -128,11 +145,10 @@ __device__ inline void lane_run(LaneWork &L, unsigned *sh32, const CountArgs &A,
 // members, s <= 32 of them): member k of the label = its k-th member in
 // ascending order; lane k returns row k of the one-word adjacency (the
 // ballot over lanes j of "member k is adjacent to member j").
-template <int NW>
+template <int NW, int RS>
 __device__ __forceinline__ uint32_t relabel_small(const uint32_t *adj, const uint32_t *wS, uint32_t *wM, int lane,
                                                   int s)
 {
-    constexpr int RS = CtaLayout<NW>::RS;
     int before = 0;
     for (int w = 0; w < NW; ++w) {
         const uint32_t sw = wS[w];
@@ -198,12 +214,12 @@ __device__ __forceinline__ void cta_unlock(int *lk)
 // A small label (s <= 32 members) found by a wide walk: relabelled into the
 // block's ring, from which any warp with free lanes takes it; into the
 // warp's own batch when the ring is full.
-template <int NW>
+template <int NW, int LNW, int RS>
 __device__ __forceinline__ void cta_push_small(CtaQueue<NW> &Q, LaneWork &L, unsigned *sh32, const CountArgs &A,
                                                int lane, int wid, LaneState &ls, LaneCounters &lc,
                                                const uint32_t *adj, int s, int h, int p)
 {
-    const uint32_t row = relabel_small<NW>(adj, Q.wS[wid], Q.wM[wid], lane, s);
+    const uint32_t row = relabel_small<LNW, RS>(adj, Q.wS[wid], Q.wM[wid], lane, s);
     int t = -1;
     if (lane == 0 && *(volatile int *)&Q.ctail - *(volatile int *)&Q.chead < CTA_CQCAP && cta_lock(&Q.lock, A.err)) {
         if (Q.ctail - Q.chead < CTA_CQCAP) t = Q.ctail++;
@@ -267,30 +283,25 @@ __device__ __forceinline__ int cta_take_small(CtaQueue<NW> &Q, LaneWork &L, int 
     return n;
 }
 
-// Walk the wide subtree of the label in queue slot `qs` (NW words, > 32
-// members) depth first over the block's shared rows; pending children on
-// the warp's stack in global memory (at most d + 1 frames of NW + 1 words).
-// The caller holds the queue lock: the slot is copied out, then released.
-// The current label lives in registers S[w] (word loops are unrolled) and in
-// the warp's wS copy (reads of word j by loop index).
-template <int NW>
-__device__ __forceinline__ void cta_dfs(CtaQueue<NW> &Q, LaneWork &L, unsigned *sh32, const CountArgs &A,
-                                        int lane, int wid, LaneState &ls, LaneCounters &lc, WalkCounters &wc,
-                                        const uint32_t *adj, uint32_t *gstk, int qs, int d)
+// One level of the walk: the subtree of label S (LNW-word bitset over the
+// rows `rows`, stride RS: the root's rows at the top level, a relabelled
+// mid-size label's at the mid level) reached with (h, p), depth first, its
+// pending children on the warp's stack `stk` in global memory (at most
+// cap + 1 frames of LNW + 1 words).  Labels of at most 32 members go to the
+// lanes (the block's ring, else the warp's own batch); at the top level a
+// label of 33..MID_D members over wider rows is relabelled to MID_NW-word
+// rows in the warp's shared memory and walked there first, and pending
+// subtrees are handed to idle warps of the block.  The current label lives
+// in registers S[w] (word loops are unrolled) and in the warp's wS copy
+// (reads of word j by loop index).
+template <int NW, int LNW, int RS, bool TOP>
+__device__ __forceinline__ void cta_level(CtaQueue<NW> &Q, CtaWarp &CW, LaneWork &L, unsigned *sh32,
+                                          const CountArgs &A, int lane, int wid, LaneState &ls, LaneCounters &lc,
+                                          WalkCounters &wc, const uint32_t *rows, uint32_t *stk, uint32_t *mstk,
+                                          uint32_t (&S)[LNW], int h, int p, int cap)
 {
-    constexpr int RS = CtaLayout<NW>::RS;
-    constexpr int FW = NW + 1;  // stack frame words: S, then (h << 16) | p
+    constexpr int FW = LNW + 1;  // stack frame words: S, then (h << 16) | p
     uint32_t *wS = Q.wS[wid], *wR = Q.wR[wid];
-    uint32_t S[NW];
-#pragma unroll
-    for (int w = 0; w < NW; ++w) S[w] = Q.S[qs][w];
-    const uint32_t hp0 = Q.hp[qs];
-    __syncwarp();
-    if (lane == 0) {
-        Q.progress += 1;
-        cta_unlock(&Q.lock);
-    }
-    int h = (int)(hp0 >> 16), p = (int)(hp0 & 0xFFFFu);
     int top = 0, bot = 0;
     unsigned clock = 0;
     const uint32_t low = (1u << lane) - 1u;
@@ -298,60 +309,92 @@ __device__ __forceinline__ void cta_dfs(CtaQueue<NW> &Q, LaneWork &L, unsigned *
     for (;;) {
         int s = 0;
 #pragma unroll
-        for (int w = 0; w < NW; ++w) s += __popc(S[w]);
+        for (int w = 0; w < LNW; ++w) s += __popc(S[w]);
 #pragma unroll
-        for (int w = 0; w < NW; ++w)
+        for (int w = 0; w < LNW; ++w)
             if (lane == w) wS[w] = S[w];
         __syncwarp();
         bool closed = true;
         if (s <= 32) {
-            cta_push_small<NW>(Q, L, sh32, A, lane, wid, ls, lc, adj, s, h, p);
+            cta_push_small<NW, LNW, RS>(Q, L, sh32, A, lane, wid, ls, lc, rows, s, h, p);
+        } else if (TOP && LNW > MID_NW && s <= MID_D) {
+            // relabel the members to 0..s-1 and walk the label over MID_NW-word rows
+            int before = 0;
+#pragma unroll
+            for (int w = 0; w < LNW; ++w) {
+                if ((S[w] >> lane) & 1u) CW.mem[before + __popc(S[w] & low)] = (uint16_t)(w * 32 + lane);
+                before += __popc(S[w]);
+            }
+            __syncwarp();
+            uint32_t mj[MID_NW];
+#pragma unroll
+            for (int q = 0; q < MID_NW; ++q) mj[q] = q * 32 + lane < s ? CW.mem[q * 32 + lane] : 0u;
+            for (int k = 0; k < s; ++k) {
+                const uint32_t mk = CW.mem[k];
+                uint32_t word = 0;
+#pragma unroll
+                for (int q = 0; q < MID_NW; ++q) {
+                    const bool bit = q * 32 + lane < s && ((rows[mj[q] * RS + (mk >> 5)] >> (mk & 31)) & 1u);
+                    const uint32_t b = __ballot_sync(FULL, bit);
+                    if (lane == q) word = b;
+                }
+                if (lane < MID_NW) CW.mid[k * MID_RS + lane] = word;
+            }
+            __syncwarp();
+            uint32_t M[MID_NW];
+#pragma unroll
+            for (int q = 0; q < MID_NW; ++q) {
+                const int bits = s - 32 * q;
+                M[q] = bits >= 32 ? FULL : (bits <= 0 ? 0u : ((1u << bits) - 1u));
+            }
+            cta_level<NW, MID_NW, MID_RS, false>(Q, CW, L, sh32, A, lane, wid, ls, lc, wc, CW.mid, mstk, nullptr, M,
+                                                 h, p, MID_D);
         } else {
             wc.nodes++;
             ++clock;
             // pivot: most neighbours inside S, ties -> lowest member index
             uint32_t best = 0, dsum = 0;
-            for (int j = 0; j < NW; ++j) {
+            for (int j = 0; j < LNW; ++j) {
                 if ((wS[j] >> lane) & 1u) {
-                    const uint32_t *row = adj + (j * 32 + lane) * RS;
+                    const uint32_t *row = rows + (j * 32 + lane) * RS;
                     uint32_t c = 0;
 #pragma unroll
-                    for (int w = 0; w < NW; ++w) c += __popc(row[w] & S[w]);
+                    for (int w = 0; w < LNW; ++w) c += __popc(row[w] & S[w]);
                     best = max(best, ((c + 1u) << 10) | (1023u - (uint32_t)(j * 32 + lane)));
                     dsum += c;
                 }
             }
             best = __reduce_max_sync(FULL, best);
             dsum = __reduce_add_sync(FULL, dsum);
-            wc.words += (unsigned long long)s * NW;
+            wc.words += (unsigned long long)s * (unsigned)((s + 31) >> 5);
             const int piv = 1023 - (int)(best & 1023u);
             if (dsum == (uint32_t)s * (uint32_t)(s - 1)) {
                 wc.leaves++;
                 if (lane == 0) lane_tally(sh32, A, h, p + s);
             } else {
-                const uint32_t *prow = adj + piv * RS;
-                uint32_t R[NW];
+                const uint32_t *prow = rows + piv * RS;
+                uint32_t R[LNW];
                 int nR = 0;
 #pragma unroll
-                for (int w = 0; w < NW; ++w) {
+                for (int w = 0; w < LNW; ++w) {
                     R[w] = S[w] & ~prow[w];
                     if (w == (piv >> 5)) R[w] &= ~(1u << (piv & 31));
                     nR += __popc(R[w]);
                 }
 #pragma unroll
-                for (int w = 0; w < NW; ++w)
+                for (int w = 0; w < LNW; ++w)
                     if (lane == w) wR[w] = R[w];
                 __syncwarp();
                 if (nR > 0 && h + 1 <= A.kmax) {
-                    if (top + nR > d + 1) {
+                    if (top + nR > cap + 1) {
                         if (bot > 0) {
                             // donated frames left room at the base: move the live ones down
-                            for (int t = lane; t < (top - bot) * FW; t += 32) gstk[t] = gstk[bot * FW + t];
+                            for (int t = lane; t < (top - bot) * FW; t += 32) stk[t] = stk[bot * FW + t];
                             top -= bot;
                             bot = 0;
                             __syncwarp();
                         }
-                        if (top + nR > d + 1) {
+                        if (top + nR > cap + 1) {
                             if (lane == 0) atomicOr(A.err, DERR_STACK);
                             return;
                         }
@@ -359,15 +402,15 @@ __device__ __forceinline__ void cta_dfs(CtaQueue<NW> &Q, LaneWork &L, unsigned *
                     // hold child of member j*32+lane: N(S, v) minus the earlier
                     // members of R; labels of at most two members close here
                     int before = 0;
-                    for (int j = 0; j < NW; ++j) {
+                    for (int j = 0; j < LNW; ++j) {
                         const uint32_t Rj = wR[j];
                         const bool inR = (Rj >> lane) & 1u;
                         bool push = inR;
-                        const uint32_t *row = adj + (j * 32 + lane) * RS;
+                        const uint32_t *row = rows + (j * 32 + lane) * RS;
                         if (inR) {
                             int cs = 0, a = 0, b = 0;
 #pragma unroll
-                            for (int w = 0; w < NW; ++w) {
+                            for (int w = 0; w < LNW; ++w) {
                                 const uint32_t bl = w < j ? R[w] : (w == j ? (Rj & low) : 0u);
                                 const uint32_t cw = row[w] & S[w] & ~bl;
                                 if (cw) {
@@ -377,26 +420,26 @@ __device__ __forceinline__ void cta_dfs(CtaQueue<NW> &Q, LaneWork &L, unsigned *
                                 cs += __popc(cw);
                             }
                             if (cs <= 2) {
-                                const bool adjp = cs == 2 && ((adj[a * RS + (b >> 5)] >> (b & 31)) & 1u);
-                                cta_close_small<false>(sh32, A, lane, cs, adjp, h + 1, p, NW, wc);
+                                const bool adjp = cs == 2 && ((rows[a * RS + (b >> 5)] >> (b & 31)) & 1u);
+                                cta_close_small<false>(sh32, A, lane, cs, adjp, h + 1, p, 1u, wc);
                                 push = false;
                             }
                         }
                         const uint32_t pushed = __ballot_sync(FULL, push);
                         if (push) {
-                            uint32_t *fr = gstk + (size_t)(top + before + __popc(pushed & low)) * FW;
+                            uint32_t *fr = stk + (size_t)(top + before + __popc(pushed & low)) * FW;
 #pragma unroll
-                            for (int w = 0; w < NW; ++w) {
+                            for (int w = 0; w < LNW; ++w) {
                                 const uint32_t bl = w < j ? R[w] : (w == j ? (Rj & low) : 0u);
                                 fr[w] = row[w] & S[w] & ~bl;
                             }
-                            fr[NW] = ((uint32_t)(h + 1) << 16) | (uint32_t)p;
+                            fr[LNW] = ((uint32_t)(h + 1) << 16) | (uint32_t)p;
                         }
                         before += __popc(pushed);
                     }
                     top += before;
                     __syncwarp();
-                    if (clock >= CTA_DONATE_EVERY) {
+                    if (TOP && clock >= CTA_DONATE_EVERY) {
                         clock = 0;
                         // a warp of the block is not walking a wide subtree: hand
                         // it our oldest pending one (the largest), if there is room
@@ -404,7 +447,7 @@ __device__ __forceinline__ void cta_dfs(CtaQueue<NW> &Q, LaneWork &L, unsigned *
                         if (lane == 0 && top - bot >= 2 && *(volatile int *)&Q.busy < warps &&
                             *(volatile int *)&Q.tail - *(volatile int *)&Q.head < CTA_QCAP) {
                             int sz = 0;
-                            for (int w = 0; w < NW; ++w) sz += __popc(gstk[bot * FW + w]);
+                            for (int w = 0; w < LNW; ++w) sz += __popc(stk[bot * FW + w]);
                             if (sz >= DONATE_MIN_WIDE && cta_lock(&Q.lock, A.err)) {
                                 give = 1;
                                 if (Q.tail - Q.head >= CTA_QCAP) {
@@ -416,8 +459,8 @@ __device__ __forceinline__ void cta_dfs(CtaQueue<NW> &Q, LaneWork &L, unsigned *
                         give = __shfl_sync(FULL, give, 0);
                         if (give) {
                             const int slot = Q.tail % CTA_QCAP;
-                            if (lane < NW) Q.S[slot][lane] = gstk[bot * FW + lane];
-                            if (lane == 0) Q.hp[slot] = gstk[bot * FW + NW];
+                            if (lane < LNW) Q.S[slot][lane] = stk[bot * FW + lane];
+                            if (lane == 0) Q.hp[slot] = stk[bot * FW + LNW];
                             __syncwarp();
                             if (lane == 0) {
                                 Q.tail += 1;
@@ -430,9 +473,9 @@ __device__ __forceinline__ void cta_dfs(CtaQueue<NW> &Q, LaneWork &L, unsigned *
                 }
                 // continue into the pivot child N(S, piv), or close it at once
                 int ps = 0, a = 0, b = 0;
-                uint32_t P[NW];
+                uint32_t P[LNW];
 #pragma unroll
-                for (int w = 0; w < NW; ++w) {
+                for (int w = 0; w < LNW; ++w) {
                     P[w] = prow[w] & S[w];
                     if (P[w]) {
                         if (ps == 0) a = w * 32 + __ffs(P[w]) - 1;
@@ -441,12 +484,12 @@ __device__ __forceinline__ void cta_dfs(CtaQueue<NW> &Q, LaneWork &L, unsigned *
                     ps += __popc(P[w]);
                 }
                 if (ps <= 2) {
-                    const bool adjp = ps == 2 && ((adj[a * RS + (b >> 5)] >> (b & 31)) & 1u);
-                    cta_close_small<true>(sh32, A, lane, ps, adjp, h, p + 1, NW, wc);
+                    const bool adjp = ps == 2 && ((rows[a * RS + (b >> 5)] >> (b & 31)) & 1u);
+                    cta_close_small<true>(sh32, A, lane, ps, adjp, h, p + 1, 1u, wc);
                 } else {
                     closed = false;
 #pragma unroll
-                    for (int w = 0; w < NW; ++w) S[w] = P[w];
+                    for (int w = 0; w < LNW; ++w) S[w] = P[w];
                     p += 1;
                 }
             }
@@ -456,12 +499,33 @@ __device__ __forceinline__ void cta_dfs(CtaQueue<NW> &Q, LaneWork &L, unsigned *
         if (top == bot) break;
         --top;
 #pragma unroll
-        for (int w = 0; w < NW; ++w) S[w] = gstk[top * FW + w];
-        const uint32_t hp = gstk[top * FW + NW];
+        for (int w = 0; w < LNW; ++w) S[w] = stk[top * FW + w];
+        const uint32_t hp = stk[top * FW + LNW];
         h = (int)(hp >> 16);
         p = (int)(hp & 0xFFFFu);
     }
     __syncwarp();
+}
+
+// Walk the wide subtree of the label in queue slot `qs` (NW words over the
+// root's rows): copied out under the caller's lock, which is then released.
+template <int NW>
+__device__ __forceinline__ void cta_dfs(CtaQueue<NW> &Q, CtaWarp &CW, LaneWork &L, unsigned *sh32,
+                                        const CountArgs &A, int lane, int wid, LaneState &ls, LaneCounters &lc,
+                                        WalkCounters &wc, const uint32_t *adj, uint32_t *gstk, int qs, int d)
+{
+    uint32_t S[NW];
+#pragma unroll
+    for (int w = 0; w < NW; ++w) S[w] = Q.S[qs][w];
+    const uint32_t hp0 = Q.hp[qs];
+    __syncwarp();
+    if (lane == 0) {
+        Q.progress += 1;
+        cta_unlock(&Q.lock);
+    }
+    uint32_t *mstk = gstk + (size_t)(d + 1) * (NW + 1);
+    cta_level<NW, NW, CtaLayout<NW>::RS, true>(Q, CW, L, sh32, A, lane, wid, ls, lc, wc, adj, gstk, mstk, S,
+                                               (int)(hp0 >> 16), (int)(hp0 & 0xFFFFu), d);
 }
 
 // The block's rows for root r (all threads): member ids, their out-list
@@ -567,10 +631,11 @@ __global__ void __launch_bounds__(32 * CTA_MAXW, 1) k_cta(CountArgs A, int dmax)
     CtaQueue<NW> &Q = *reinterpret_cast<CtaQueue<NW> *>(smem);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, warps = blockDim.x >> 5;
     LaneWork *lw = reinterpret_cast<LaneWork *>(smem + sizeof(CtaQueue<NW>));
-    unsigned *sh32 = reinterpret_cast<unsigned *>(lw + warps);
+    CtaWarp *cw = reinterpret_cast<CtaWarp *>(lw + warps);
+    unsigned *sh32 = reinterpret_cast<unsigned *>(cw + warps);
     uint32_t *adj = sh32 + HIST_H * HIST_P;
     LaneWork &L = lw[wid];
-    const size_t stack_words = (size_t)(dmax + 1) * (NW + 1);
+    const size_t stack_words = CtaLayout<NW>::stack_words(dmax);
     uint32_t *gstk = A.gstack + (size_t)(blockIdx.x * warps + wid) * stack_words;
     uint32_t *gscratch = A.gstack + (size_t)gridDim.x * warps * stack_words +
                          (size_t)blockIdx.x * CtaLayout<NW>::gather_words(dmax);
@@ -636,7 +701,7 @@ __global__ void __launch_bounds__(32 * CTA_MAXW, 1) k_cta(CountArgs A, int dmax)
             took = __shfl_sync(FULL, took, 0);
             if (took < 0) break;
             if (took > 0) {
-                cta_dfs<NW>(Q, L, sh32, A, lane, wid, ls, lc, wc, adj, gstk, took - 1, d);
+                cta_dfs<NW>(Q, cw[wid], L, sh32, A, lane, wid, ls, lc, wc, adj, gstk, took - 1, d);
                 wc.fold();
                 __syncwarp();
                 if (lane == 0) {

@@ -225,7 +225,8 @@ __device__ __forceinline__ void tally_lane(unsigned long long *shist, const Coun
 // single member or an adjacent pair is a clique, one leaf (h, p + |S'|); a
 // non-adjacent pair {a < b} takes a as pivot (a pivot leaf (h, p + 1)) and
 // holds b (a leaf (h + 1, p), cut when h + 1 > kmax).  Counts the nodes,
-// leaves and pivot words (wpm per member) the walk would have spent.
+// leaves and pivot words (wpm per member: 1, a label of at most two members
+// fits one word) the walk would have spent.
 // UNIFORM: every lane calls with the same arguments, lane 0 tallies.
 template <bool SHIST, bool UNIFORM>
 __device__ __forceinline__ void close_small(unsigned long long *shist, const CountArgs &A, int lane, int cs,
@@ -808,7 +809,7 @@ __device__ void walk_root(WarpWork<NW> &Wk, unsigned long long *shist, const Cou
             }
             best = __reduce_max_sync(FULL, best);
             dsum = __reduce_add_sync(FULL, dsum);
-            wc.words += (unsigned long long)s * NW;
+            wc.words += (unsigned long long)s * (unsigned)((s + 31) >> 5);
             const int piv = 1023 - (int)(best & 1023u);
             if (dsum == (uint32_t)s * (uint32_t)(s - 1)) {
                 // S is a clique: one leaf with |S| more pivot links
@@ -867,7 +868,7 @@ __device__ void walk_root(WarpWork<NW> &Wk, unsigned long long *shist, const Cou
                             }
                             if (cs <= 2) {
                                 const bool adj = cs == 2 && ((Wk.adj[a * RS + (b >> 5)] >> (b & 31)) & 1u);
-                                close_small<SHIST, false>(shist, A, lane, cs, adj, h + 1, p, NW, wc);
+                                close_small<SHIST, false>(shist, A, lane, cs, adj, h + 1, p, 1u, wc);
                                 push = false;
                             }
                         }
@@ -916,7 +917,7 @@ __device__ void walk_root(WarpWork<NW> &Wk, unsigned long long *shist, const Cou
                 }
                 if (MODE == MODE_GLOBAL && ps <= 2) {
                     const bool adj = ps == 2 && ((Wk.adj[a * RS + (b >> 5)] >> (b & 31)) & 1u);
-                    close_small<SHIST, true>(shist, A, lane, ps, adj, h, p + 1, NW, wc);
+                    close_small<SHIST, true>(shist, A, lane, ps, adj, h, p + 1, 1u, wc);
                 } else {
                     closed = false;
 #pragma unroll

@@ -13,7 +13,7 @@ static pvt_status launch_cta_nw(pvt_dag *g, CountArgs A, int cls, int dmax, cuda
     int optin = 0;
     PVT_CK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, g->device));
     const size_t fixed = Lay::bytes(0, dmax);
-    int warps = fixed < (size_t)optin ? (int)(((size_t)optin - fixed) / sizeof(LaneWork)) : 0;
+    int warps = fixed < (size_t)optin ? (int)(((size_t)optin - fixed) / (sizeof(LaneWork) + sizeof(CtaWarp))) : 0;
     warps = std::min(warps, CTA_MAXW);
     if (warps < 1) {
         set_error("CTA walk: shared memory too small for out-degree " + std::to_string(dmax));
@@ -29,7 +29,7 @@ static pvt_status launch_cta_nw(pvt_dag *g, CountArgs A, int cls, int dmax, cuda
     }
     const unsigned blocks = std::max(1u, std::min<unsigned>((unsigned)(g->num_sms * per_sm), A.nroots));
     pvt_status st =
-        grow(g->gstack[cls], (size_t)blocks * warps * (dmax + 1) * (NW + 1) + (size_t)blocks * Lay::gather_words(dmax), s);
+        grow(g->gstack[cls], (size_t)blocks * warps * Lay::stack_words(dmax) + (size_t)blocks * Lay::gather_words(dmax), s);
     if (st != PVT_OK) return st;
     A.gstack = g->gstack[cls].p;
     phase_begin(g, 1 + cls, s);
