@@ -48,8 +48,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-sequential", action="store_true", help="skip the one-core oracle run of the CPU baseline")
     ap.add_argument("--no-local", action="store_true", help="skip the per-vertex / per-edge measurement")
-    ap.add_argument("--serving-queries", type=int, default=300,
-                    help="queries in the serving stream (the full stream is 10000); 0 skips serving")
+    ap.add_argument("--serving-queries", type=int, default=10000,
+                    help="queries in the serving stream (10000 by default); 0 skips serving")
     return ap.parse_args()
 
 
@@ -269,21 +269,33 @@ def torch_flush(dev):
 def serving_stream(q, seed=5):
     """Query stream: independent ER or Chung-Lu graphs, n log-uniform in
     [100, 50000], average degree U[5, 60], exponent U[2.0, 2.5]; each asks
-    global all-k or per-edge counts with probability 1/2."""
+    global all-k or per-edge counts with probability 1/2.  The parameters are
+    drawn in order from one seeded generator; the graphs are then generated
+    on host threads (the generator runs outside the interpreter lock)."""
+    import concurrent.futures as cf
     from paper_2001_06784_gb300 import graphgen
     rng = np.random.default_rng(seed)
-    out = []
+    spec = []
     for i in range(q):
         n = int(np.exp(rng.uniform(np.log(100), np.log(50000))))
         deg = float(rng.uniform(5, 60))
         kind = "global" if rng.random() < 0.5 else "edge"
         if rng.random() < 0.5:
-            rp, col = graphgen.generate(n, er_avg_deg=min(deg, n - 1), seed=5_000_000 + i)
+            spec.append((i, n, "er", min(deg, n - 1), None, kind))
         else:
             m = max(1, min(int(n * deg / 2), n * (n - 1) // 4))
-            rp, col = graphgen.generate(n, chung_lu=(m, float(rng.uniform(2.0, 2.5))), seed=5_000_000 + i)
-        out.append((rp, col, kind))
-    return out
+            spec.append((i, n, "cl", m, float(rng.uniform(2.0, 2.5)), kind))
+
+    def make(sp):
+        i, n, kind_g, a, beta, kind = sp
+        if kind_g == "er":
+            rp, col = graphgen.generate(n, er_avg_deg=a, seed=5_000_000 + i)
+        else:
+            rp, col = graphgen.generate(n, chung_lu=(a, beta), seed=5_000_000 + i)
+        return rp, col, kind
+
+    with cf.ThreadPoolExecutor(max_workers=os.cpu_count() or 4) as ex:
+        return list(ex.map(make, spec))
 
 
 def run_local(args, dev, flush):
@@ -390,35 +402,76 @@ def run_graph_replay(args, dev, reps=50):
 
 
 def run_serving(args, dev):
-    """p50/p99 latency of the query server (continuous batching) against one
-    launch sequence per graph, on the same Poisson arrivals."""
+    """The query server (continuous batching, large queries on the whole-GPU
+    direct path beside the batches) against one launch sequence per graph, on
+    the same query stream: closed-loop saturation throughput of each form
+    (every query submitted at once / one after another), then p50/p99
+    latency with Poisson arrivals at 0.8 x the plain form's saturation rate.
+    Every served result is checked word for word against the plain form's
+    (SHA-1 of the words), and the smallest queries against the oracle."""
+    import hashlib
     import threading as th
     import torch
     import paper_2001_06784_gb300 as pvt
     qs = serving_stream(args.serving_queries)
     edges = sum(len(c) // 2 for _, c, _ in qs)
 
+    def digest(a):
+        return hashlib.sha1(np.ascontiguousarray(a).view(np.uint8)).hexdigest()
+
     def plain_one(rp, col, kind):
         rpd = torch.from_numpy(rp).to(dev, non_blocking=True)
         cd = torch.from_numpy(col.view(np.int32)).to(dev, non_blocking=True)
         dag = pvt.orient(rpd, cd)
         out = dag.count_global() if kind == "global" else dag.count_local_edge()
-        host = out.cpu()
+        host = out.cpu().numpy().view(np.uint64)
         dag.free()
-        return host
+        return host.reshape((1,) + host.shape) if kind == "global" else host
 
     for rp, col, kind in qs[:3]:  # warm-up
         plain_one(rp, col, kind)
     torch.cuda.synchronize(dev)
+    # ---- closed loop, plain: one query after another
+    plain_hash = []
     t0 = time.perf_counter()
     for rp, col, kind in qs:
-        plain_one(rp, col, kind)
-    sat_s = time.perf_counter() - t0
-    sat_qps = len(qs) / sat_s
+        plain_hash.append(digest(plain_one(rp, col, kind)))
+    sat_plain_s = time.perf_counter() - t0
+    sat_qps = len(qs) / sat_plain_s
     lam = 0.8 * sat_qps
     arrivals = np.cumsum(np.random.default_rng(55).exponential(1.0 / lam, len(qs)))
+    small = sorted(range(len(qs)), key=lambda i: len(qs[i][1]))[:8]
+    kept = {}
+    cfg = dict(mem_budget=64 << 30, max_inflight=4096, max_batch=256, streams=4)
+    with pvt.Server(**cfg) as sv:
+        for rp, col, kind in qs[:3]:  # warm-up
+            t = sv.submit(rp, col, kind)
+            sv.wait(t)
+            sv.result(t)
+        # ---- closed loop, served: every query submitted at once
+        served_hash = [None] * len(qs)
+        t0 = time.perf_counter()
+        tickets = [sv.submit(rp, col, kind) for rp, col, kind in qs]
+        for i, t in enumerate(tickets):
+            sv.wait(t)
+            words, _ = sv.result(t)
+            served_hash[i] = digest(words)
+            if i in small:
+                kept[i] = words
+        sat_srv_s = time.perf_counter() - t0
+    mismatch = sum(a != b for a, b in zip(plain_hash, served_hash))
+    # oracle on the smallest queries
+    import oracle
+    oracle_ok = True
+    for i in small:
+        rp, col, kind = qs[i]
+        K = kept[i].shape[1] - 1
+        ref = oracle.count(rp, col, kmax=K, edge=kind == "edge")
+        want = ref["C"] if kind == "global" else oracle.to_int(ref["ce"])
+        got = pvt.to_ints(kept[i][0]) if kind == "global" else pvt.to_ints(kept[i])
+        oracle_ok = oracle_ok and got == want
 
-    # plain, replayed in real time: one query at a time in arrival order
+    # ---- open loop, plain: replayed in real time, one query at a time
     lat_plain = []
     t0 = time.perf_counter()
     for (rp, col, kind), ta in zip(qs, arrivals):
@@ -429,10 +482,10 @@ def run_serving(args, dev):
         lat_plain.append(time.perf_counter() - t0 - ta)
     plain_span = time.perf_counter() - t0
 
-    # batched server: a submitter thread keeps the arrivals, latency is
+    # ---- open loop, served: a submitter thread keeps the arrivals, latency
     # measured inside the server (submit -> result ready)
     lat_srv = [None] * len(qs)
-    with pvt.Server(mem_budget=64 << 30, max_inflight=4096, max_batch=256, streams=4) as sv:
+    with pvt.Server(**cfg) as sv:
         for rp, col, kind in qs[:3]:  # warm-up
             t = sv.submit(rp, col, kind)
             sv.wait(t)
@@ -464,8 +517,14 @@ def run_serving(args, dev):
 
     return {"queries": len(qs), "stream": "ER or Chung-Lu, n log-uniform 100..50000, avg deg U[5,60], "
                                           "global or per-edge (1/2 each), Poisson arrivals, seed 5",
-            "saturation_qps_plain": sat_qps, "arrival_rate_qps": lam, "edges_total": edges,
-            "plain": summary(lat_plain, plain_span), "batched": summary(lat_srv, srv_span)}
+            "edges_total": edges,
+            "saturation": {"plain_qps": sat_qps, "served_qps": len(qs) / sat_srv_s,
+                           "plain_edges_per_s": edges / sat_plain_s, "served_edges_per_s": edges / sat_srv_s,
+                           "form": "closed loop: plain one query after another; served all submitted at once"},
+            "arrival_rate_qps": lam,
+            "plain": summary(lat_plain, plain_span), "batched": summary(lat_srv, srv_span),
+            "check": {"served_vs_plain_mismatches": int(mismatch), "oracle_sample": len(small),
+                      "oracle_sample_ok": bool(oracle_ok)}}
 
 
 def main():

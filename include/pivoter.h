@@ -385,7 +385,10 @@ pvt_status pvt_count_global_noalloc(int64_t n, const int64_t *orow, const uint32
  * launch (one block per graph), and walks the roots of the whole group in
  * shared persistent launches; a later group is admitted and oriented while
  * earlier groups still run, and groups run on separate streams so their work
- * overlaps.  Results are exact and equal to the single-graph entry points.
+ * overlaps.  Queries of at least direct_edges edges bypass the batches: a
+ * second worker runs them one at a time through pvt_orient and the count
+ * entry points on a stream of its own, whole-GPU kernels beside the batches.
+ * Results are exact and equal to the single-graph entry points.
  */
 typedef struct pvt_server pvt_server;
 
@@ -394,6 +397,10 @@ typedef struct pvt_server_config {
     int32_t max_inflight;  /* requests admitted at once (0: 1024) */
     int32_t max_batch;     /* graphs per batched launch (0: 256) */
     int32_t streams;       /* concurrent batches (0: 4) */
+    int64_t direct_edges;  /* queries with at least this many edges run alone on
+                              the whole GPU (the single-graph entry points, in
+                              a worker of their own) instead of in a batch;
+                              0: 65536, < 0: never */
 } pvt_server_config;
 
 enum { PVT_QUERY_GLOBAL = 0, PVT_QUERY_VERTEX = 1, PVT_QUERY_EDGE = 2 };
@@ -404,7 +411,8 @@ pvt_status pvt_server_create(const pvt_server_config *cfg, pvt_server **out);
 /*
  * Submit one query: host CSR (as for pvt_orient; copied before return, so the
  * caller may reuse its buffers), kind PVT_QUERY_*, kmax < 0 for every k
- * (alpha + 1).  n must be below 2^32 and the graph's degeneracy at most 512.
+ * (alpha + 1).  n must be below 2^32 and the degeneracy at most 512 (1024 for
+ * queries on the direct path).
  * ticket receives the query's handle.  Errors: PVT_EINVAL, PVT_ENOMEM (the
  * query can never fit in mem_budget).
  */

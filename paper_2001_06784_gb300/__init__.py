@@ -239,8 +239,8 @@ class Server:
     KINDS = {"global": _lib.QUERY_GLOBAL, "vertex": _lib.QUERY_VERTEX, "edge": _lib.QUERY_EDGE}
 
     def __init__(self, mem_budget: int = 8 << 30, max_inflight: int = 1024, max_batch: int = 256,
-                 streams: int = 4):
-        cfg = _lib.ServerConfig(int(mem_budget), int(max_inflight), int(max_batch), int(streams))
+                 streams: int = 4, direct_edges: int = 0):
+        cfg = _lib.ServerConfig(int(mem_budget), int(max_inflight), int(max_batch), int(streams), int(direct_edges))
         h = ctypes.c_void_p()
         _lib.check(_lib.lib().pvt_server_create(ctypes.byref(cfg), ctypes.byref(h)))
         self._h = h

@@ -37,7 +37,7 @@ class Policy(ctypes.Structure):
 class ServerConfig(ctypes.Structure):
     """pvt_server_config (include/pivoter.h)."""
     _fields_ = [("mem_budget", ctypes.c_size_t), ("max_inflight", ctypes.c_int32),
-                ("max_batch", ctypes.c_int32), ("streams", ctypes.c_int32)]
+                ("max_batch", ctypes.c_int32), ("streams", ctypes.c_int32), ("direct_edges", ctypes.c_int64)]
 
 
 QUERY_GLOBAL, QUERY_VERTEX, QUERY_EDGE = 0, 1, 2

@@ -76,6 +76,7 @@ private:
 
 struct Request {
     uint64_t ticket = 0;
+    bool direct = false;             // whole-GPU single-graph path
     int kind = 0, kmax_req = -1;
     int64_t n = 0, nnz = 0, m = 0;
     std::vector<int64_t> rp;
@@ -140,6 +141,9 @@ struct pvt_server {
     std::mutex mu;
     std::condition_variable cv_work, cv_done, cv_complete;
     std::deque<ReqPtr> pending;
+    std::deque<ReqPtr> pending_direct;  // queries for the whole-GPU path
+    std::thread direct_worker;
+    cudaStream_t direct_stream = nullptr;
     std::map<uint64_t, ReqPtr> all;
     std::deque<Batch *> running;
     size_t mem_used = 0;
@@ -362,6 +366,90 @@ void run_group(pvt_server *sv, std::vector<ReqPtr> &group)
     sv->cv_complete.notify_all();
 }
 
+// One query through the single-graph entry points on the direct stream:
+// copy the CSR, orient, count into device memory, copy the words to pinned
+// host memory; the worker waits for it before the next direct query.
+void run_direct(pvt_server *sv, const ReqPtr &rp)
+{
+    Request &r = *rp;
+    cudaStream_t s = sv->direct_stream;
+    const size_t n = (size_t)r.n;
+    void *base = nullptr;
+    if (cudaMallocAsync(&base, align_up(8 * (n + 1)) + align_up(4 * std::max<int64_t>(r.nnz, 1)), s) != cudaSuccess) {
+        fail_request(sv, rp, PVT_ENOMEM, "server: device allocation failed");
+        return;
+    }
+    r.dallocs.push_back(base);
+    char *p = static_cast<char *>(base);
+    int64_t *d_rp = carve<int64_t>(p, n + 1);
+    uint32_t *d_col = carve<uint32_t>(p, (size_t)r.nnz);
+    cudaMemcpyAsync(d_rp, r.rp.data(), 8 * (n + 1), cudaMemcpyHostToDevice, s);
+    if (r.nnz) cudaMemcpyAsync(d_col, r.col.data(), 4 * (size_t)r.nnz, cudaMemcpyHostToDevice, s);
+    pvt_dag *dag = nullptr;
+    int32_t alpha = 0;
+    pvt_status st = pvt_orient(r.n, r.nnz, d_rp, r.nnz ? d_col : nullptr, 0, s, &dag, &alpha);
+    if (st != PVT_OK) {
+        fail_request(sv, rp, st, "server: " + std::string(pvt_last_error()));
+        return;
+    }
+    r.alpha = alpha;
+    r.W = min_words(r.n, alpha);
+    r.K = (r.kmax_req >= 0 ? r.kmax_req : alpha + 1) + 1;
+    r.rows = r.kind == PVT_QUERY_GLOBAL ? 1 : (r.kind == PVT_QUERY_VERTEX ? r.n : r.m);
+    const size_t words = (size_t)r.rows * r.K * r.W;
+    void *out = nullptr;
+    r.hres = static_cast<uint64_t *>(sv->pinned.get(8 * std::max<size_t>(words, 1), &r.hres_cls));
+    if (!r.hres || cudaMallocAsync(&out, 8 * std::max<size_t>(words, 1), s) != cudaSuccess) {
+        pvt_dag_free(dag);
+        fail_request(sv, rp, PVT_ENOMEM, "server: result allocation failed");
+        return;
+    }
+    r.dallocs.push_back(out);
+    uint64_t *o = static_cast<uint64_t *>(out);
+    st = r.kind == PVT_QUERY_GLOBAL   ? pvt_count_global(dag, r.K - 1, r.W, o, s)
+         : r.kind == PVT_QUERY_VERTEX ? pvt_count_local_vertex(dag, r.K - 1, r.W, o, s)
+                                      : pvt_count_local_edge(dag, r.K - 1, r.W, o, s);
+    const std::string err = st == PVT_OK ? std::string() : std::string(pvt_last_error());
+    if (st == PVT_OK) cudaMemcpyAsync(r.hres, o, 8 * words, cudaMemcpyDeviceToHost, s);
+    const cudaError_t ce = cudaStreamSynchronize(s);
+    pvt_dag_free(dag);
+    if (st != PVT_OK || ce != cudaSuccess) {
+        fail_request(sv, rp, st != PVT_OK ? st : PVT_ECUDA, "server: " + (st != PVT_OK ? err : cudaGetErrorString(ce)));
+        return;
+    }
+    for (void *q : r.dallocs) cudaFreeAsync(q, s);
+    std::lock_guard<std::mutex> lk(sv->mu);
+    r.dallocs.clear();
+    r.t_done = Clock::now();
+    r.state = REQ_DONE;
+    sv->mem_used -= r.reserve;
+    sv->inflight -= 1;
+    sv->cv_done.notify_all();
+    sv->cv_work.notify_all();
+}
+
+void direct_main(pvt_server *sv)
+{
+    cudaSetDevice(sv->device);
+    for (;;) {
+        ReqPtr r;
+        {
+            std::unique_lock<std::mutex> lk(sv->mu);
+            sv->cv_work.wait(lk, [&] {
+                return sv->stop || (!sv->pending_direct.empty() && can_admit(sv, *sv->pending_direct.front()));
+            });
+            if (sv->pending_direct.empty() && sv->stop) break;
+            if (sv->pending_direct.empty() || !can_admit(sv, *sv->pending_direct.front())) continue;
+            r = sv->pending_direct.front();
+            sv->pending_direct.pop_front();
+            sv->mem_used += r->reserve;
+            sv->inflight += 1;
+            r->state = REQ_RUNNING;
+        }
+        run_direct(sv, r);
+    }
+}
+
 void worker_main(pvt_server *sv)
 {
     cudaSetDevice(sv->device);
@@ -371,6 +459,7 @@ void worker_main(pvt_server *sv)
             std::unique_lock<std::mutex> lk(sv->mu);
             sv->cv_work.wait(lk, [&] { return sv->stop || (!sv->pending.empty() && can_admit(sv, *sv->pending.front())); });
             if (sv->pending.empty() && sv->stop) break;
+            if (sv->pending.empty()) continue;
             while (!sv->pending.empty() && (int)group.size() < sv->cfg.max_batch && can_admit(sv, *sv->pending.front())) {
                 ReqPtr r = sv->pending.front();
                 sv->pending.pop_front();
@@ -418,7 +507,10 @@ void completer_main(pvt_server *sv)
         std::vector<Batch *> snapshot;
         {
             std::unique_lock<std::mutex> lk(sv->mu);
-            sv->cv_complete.wait(lk, [&] { return !sv->running.empty() || (sv->stop && sv->inflight == 0 && sv->pending.empty()); });
+            sv->cv_complete.wait(lk, [&] {
+                return !sv->running.empty() ||
+                       (sv->stop && sv->inflight == 0 && sv->pending.empty() && sv->pending_direct.empty());
+            });
             if (sv->running.empty()) break;
             snapshot.assign(sv->running.begin(), sv->running.end());
         }
@@ -459,9 +551,11 @@ pvt_status pvt_server_create(const pvt_server_config *cfg, pvt_server **out)
     if (sv->cfg.max_inflight <= 0) sv->cfg.max_inflight = 1024;
     if (sv->cfg.max_batch <= 0) sv->cfg.max_batch = 256;
     if (sv->cfg.streams <= 0) sv->cfg.streams = 4;
+    if (sv->cfg.direct_edges == 0) sv->cfg.direct_edges = 65536;
     cudaError_t e = cudaGetDevice(&sv->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sv->num_sms, cudaDevAttrMultiProcessorCount, sv->device);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&sv->orient_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&sv->direct_stream, cudaStreamNonBlocking);
     for (int i = 0; i < sv->cfg.streams && e == cudaSuccess; ++i) {
         cudaStream_t s;
         e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
@@ -480,6 +574,7 @@ pvt_status pvt_server_create(const pvt_server_config *cfg, pvt_server **out)
         pvt_status st = cuda_fail(e, "pvt_server_create");
         for (cudaStream_t s : sv->walk_streams) cudaStreamDestroy(s);
         if (sv->orient_stream) cudaStreamDestroy(sv->orient_stream);
+        if (sv->direct_stream) cudaStreamDestroy(sv->direct_stream);
         cudaFree(sv->binom);
         cudaFree(sv->binom_err);
         delete sv;
@@ -487,6 +582,7 @@ pvt_status pvt_server_create(const pvt_server_config *cfg, pvt_server **out)
     }
     sv->worker = std::thread(worker_main, sv);
     sv->completer = std::thread(completer_main, sv);
+    sv->direct_worker = std::thread(direct_main, sv);
     *out = sv;
     return PVT_OK;
 }
@@ -507,8 +603,10 @@ pvt_status pvt_server_submit(pvt_server *sv, int64_t n, int64_t nnz, const int64
     r->m = nnz / 2;
     r->rp.assign(row_ptr, row_ptr + n + 1);
     r->col.assign(col, col + nnz);
+    r->direct = sv->cfg.direct_edges > 0 && r->m >= sv->cfg.direct_edges;
     const int ab = alpha_bound(*r);
-    r->reserve = estimate_bytes(*r, ab);
+    // the direct path's dag also holds its own scratch (frame buffer, queues)
+    r->reserve = estimate_bytes(*r, ab) + (r->direct ? ((size_t)256 << 20) : 0);
     if (r->reserve > sv->cfg.mem_budget) {
         set_error("pvt_server_submit: query needs more device memory than the server's budget");
         return PVT_ENOMEM;
@@ -522,7 +620,7 @@ pvt_status pvt_server_submit(pvt_server *sv, int64_t n, int64_t nnz, const int64
         }
         r->ticket = sv->next_ticket++;
         sv->all[r->ticket] = r;
-        sv->pending.push_back(r);
+        (r->direct ? sv->pending_direct : sv->pending).push_back(r);
     }
     sv->cv_work.notify_all();
     *ticket = r->ticket;
@@ -607,6 +705,7 @@ void pvt_server_destroy(pvt_server *sv)
     }
     sv->cv_work.notify_all();
     if (sv->worker.joinable()) sv->worker.join();
+    if (sv->direct_worker.joinable()) sv->direct_worker.join();
     {
         std::lock_guard<std::mutex> lk(sv->mu);
         sv->cv_complete.notify_all();
@@ -617,6 +716,7 @@ void pvt_server_destroy(pvt_server *sv)
         if (kv.second->hres) sv->pinned.put(kv.second->hres, kv.second->hres_cls);
     for (cudaStream_t s : sv->walk_streams) cudaStreamDestroy(s);
     cudaStreamDestroy(sv->orient_stream);
+    cudaStreamDestroy(sv->direct_stream);
     cudaFree(sv->binom);
     cudaFree(sv->binom_err);
     delete sv;

@@ -32,10 +32,13 @@ def mixed_graphs():
     return out
 
 
-def test_server_mix_equals_alone_and_oracle():
+@pytest.mark.parametrize("direct_edges", [-1, 3000, 0])
+def test_server_mix_equals_alone_and_oracle(direct_edges):
+    """direct_edges: -1 batches every query; 3000 sends most of them down the
+    whole-GPU direct path beside the batches; 0 is the default threshold."""
     import paper_2001_06784_gb300 as pvt
     qs = mixed_graphs()
-    with pvt.Server(mem_budget=4 << 30, max_batch=16, streams=3) as sv:
+    with pvt.Server(mem_budget=4 << 30, max_batch=16, streams=3, direct_edges=direct_edges) as sv:
         # all at once (they batch and overlap)
         tickets = [sv.submit(rp, col, kind) for rp, col, kind in qs]
         mixed = [sv.result(t)[0] for t in tickets if sv.wait(t, 60000)]
