@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-sequential", action="store_true", help="skip the one-core oracle run of the CPU baseline")
     ap.add_argument("--no-local", action="store_true", help="skip the per-vertex / per-edge measurement")
+    ap.add_argument("--no-cl3m", action="store_true",
+                    help="skip the all-k count of the 128M-edge com-orkut-shaped graph (about 100 s)")
     ap.add_argument("--serving-queries", type=int, default=10000,
                     help="queries in the serving stream (10000 by default); 0 skips serving")
     return ap.parse_args()
@@ -362,6 +364,75 @@ def run_local(args, dev, flush):
         res[kind]["distribution"] = dist
         del out, t
     return res
+
+
+def run_cl3m(args, dev):
+    """All-k global counts of the com-orkut-shaped graph (Chung-Lu n = 3M,
+    m ~ 128M, exponent 2.0, 2,000 planted communities of 50-120 vertices at
+    density 0.8; degeneracy 733): one orient + count_global on the graph
+    already in HBM, timed with CUDA events, phases with the classes run one
+    after another.  Its tree holds about 1.1e12 nodes, so a count takes on
+    the order of 100 s: it is timed once, not K + W times.  Checks: C_1 = n,
+    C_2 = m and C_3 = the oracle's triangle enumeration (plain definition,
+    no SCT), word for word; every count is exact by construction (the
+    device's root-path check ran)."""
+    import torch
+    import paper_2001_06784_gb300 as pvt
+    from paper_2001_06784_gb300 import graphgen
+    import oracle
+    name = "cl3m_m117m_b2.0_comm2000"
+    rp, col = graphgen.workload(name)
+    n, m = len(rp) - 1, len(col) // 2
+    rpd = torch.from_numpy(rp).to(dev)
+    cd = torch.from_numpy(col.view(np.int32)).to(dev)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch_flush(dev)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    sampler = ClockSampler(int(str(dev).split(":")[-1]) if ":" in str(dev) else 0)
+    sampler.start()
+    e0.record(stream)
+    dag = pvt.orient(rpd, cd, profile=True)
+    so = dag.stats()
+    dag.set_policy(serial=True)
+    C = dag.count_global()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1)
+    st = dag.stats()
+    words = pvt.to_ints(C)
+    depths = dag.leaf_depths()
+    dag.free()
+    del flush
+    omega = max(k for k, c in enumerate(words) if c)
+    T = oracle.triangles(rp, col, threads=os.cpu_count() or 1)
+    ph = dict(st["ms"])
+    ph["peel"], ph["orient"] = so["ms"]["peel"], so["ms"]["orient"]
+    try:
+        alu = pvt.measure_popc_rate(dev) / 1e9
+    except Exception:
+        alu = POPC_PER_CLK_PER_SM * SM_COUNT * SM_MAX_MHZ * 1e6 / 1e9
+    names = pvt.Dag.PHASES
+    kern = []
+    for c in range(1, 7):
+        t = ph[names[1 + c]]
+        if t > 0:
+            a = st["class_words"][c] / (t / 1000.0) / 1e9
+            kern.append({"kernel": names[1 + c], "ms": t, "algorithmic": st["class_words"][c], "achieved": a,
+                         "unit": "Gop/s", "frac": a / alu, "roots": st["roots"][c]})
+    dom = max(kern, key=lambda k: k["ms"])
+    return {"workload": name, "n": n, "m": m, "alpha": len(depths) - 2, "omega": omega, "kmax": len(words) - 1,
+            "ms": ms, "edges_per_s": m / (ms / 1000.0), "counts": {"C1": words[1], "C2": words[2], "C3": words[3],
+                                                                  "C_max": str(max(words))},
+            "checks": {"C1_is_n": words[1] == n, "C2_is_m": words[2] == m, "C3_is_oracle_triangles": words[3] == T},
+            "sct": {"nodes": st["sct_nodes"], "leaves": st["sct_leaves"], "pivot_words": st["pivot_words"],
+                    "leaf_depth_mode": int(np.argmax(depths))},
+            "phases_ms": ph, "kernels": kern,
+            "roofline": {"bound": "alu", "kernel": dom["kernel"], "achieved": dom["achieved"], "peak": alu,
+                         "unit": "Gop/s", "frac": dom["frac"]},
+            "clocks": clocks,
+            "timing": "one orient + all-k count, CUDA events, classes serialised (policy.serial)"}
 
 
 def run_graph_replay(args, dev, reps=50):
@@ -681,6 +752,11 @@ def main():
     # ---- local counts (per-vertex, per-edge) on the 500k-vertex graph
     if rank == 0 and not args.no_local:
         out["local"] = run_local(args, dev, flush)
+
+    # ---- all-k counts of the 128M-edge com-orkut-shaped graph, timed once
+    if rank == 0 and not args.no_cl3m:
+        del flush
+        out["cl3m_allk"] = run_cl3m(args, dev)
 
     # ---- serving: Poisson stream of independent queries (rank 0 only)
     if rank == 0 and args.serving_queries > 0:

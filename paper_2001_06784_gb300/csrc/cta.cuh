@@ -31,6 +31,10 @@ constexpr unsigned long long CTA_LOCK_LIMIT_NS = 2000000000ull;  // 2 s for the 
 // MID_NW words (in the warp's shared memory) and walked there: a pivot word
 // pair then costs a 4-word row instead of the root's NW words.
 constexpr int MID_NW = 4, MID_RS = 5, MID_D = 32 * MID_NW;
+// ... when at least this many hold levels may still follow (kmax - h): the
+// relabelling costs up to |S| * MID_NW ballots, which a subtree cut a level
+// or two further down does not pay back
+constexpr int CTA_MID_DEPTH = 3;
 
 // Per-warp shared state of the CTA walk beside its lane batch: the rows of a
 // relabelled mid-size label and the member list of a label being relabelled.
@@ -290,7 +294,8 @@ __device__ __forceinline__ int cta_take_small(CtaQueue<NW> &Q, LaneWork &L, int 
 // cap + 1 frames of LNW + 1 words).  Labels of at most 32 members go to the
 // lanes (the block's ring, else the warp's own batch); at the top level a
 // label of 33..MID_D members over wider rows is relabelled to MID_NW-word
-// rows in the warp's shared memory and walked there first, and pending
+// rows in the warp's shared memory and walked there first (unless kmax
+// truncates its subtree within CTA_MID_DEPTH hold levels), and pending
 // subtrees are handed to idle warps of the block.  The current label lives
 // in registers S[w] (word loops are unrolled) and in the warp's wS copy
 // (reads of word j by loop index).
@@ -317,7 +322,7 @@ __device__ __forceinline__ void cta_level(CtaQueue<NW> &Q, CtaWarp &CW, LaneWork
         bool closed = true;
         if (s <= 32) {
             cta_push_small<NW, LNW, RS>(Q, L, sh32, A, lane, wid, ls, lc, rows, s, h, p);
-        } else if (TOP && LNW > MID_NW && s <= MID_D) {
+        } else if (TOP && LNW > MID_NW && s <= MID_D && A.kmax - h >= CTA_MID_DEPTH) {
             // relabel the members to 0..s-1 and walk the label over MID_NW-word rows
             int before = 0;
 #pragma unroll
