@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-sequential", action="store_true", help="skip the one-core oracle run of the CPU baseline")
     ap.add_argument("--no-local", action="store_true", help="skip the per-vertex / per-edge measurement")
+    ap.add_argument("--profile", default=None, choices=["lanes", "cta", "local", "peel"],
+                    help="run one small case of one kernel family for a profiler and exit (no JSON line)")
     ap.add_argument("--no-cl3m", action="store_true",
                     help="skip the all-k count of the 128M-edge com-orkut-shaped graph (about 100 s)")
     ap.add_argument("--serving-queries", type=int, default=10000,
@@ -598,11 +600,48 @@ def run_serving(args, dev):
                       "oracle_sample_ok": bool(oracle_ok)}}
 
 
+def run_profile_case(args, dev):
+    """One small case per kernel family, for ncu (`--profile`):
+    lanes  orient + global count of the bench graph (the frame phase, k_lanes)
+    cta    orient the 128M-edge graph, then the roots with ids below 20,000
+           (a range that holds heavy roots), kmax = 5 (k_cta)
+    local  per-vertex and per-edge tables of the 500k-vertex graph, k <= 12
+           (k_count in MODE_VERTEX / MODE_EDGE)
+    peel   orient the bench graph (k_peel, k_peel_tail)"""
+    import torch
+    import paper_2001_06784_gb300 as pvt
+    from paper_2001_06784_gb300 import graphgen
+    name = {"lanes": DEFAULT_WORKLOAD, "peel": DEFAULT_WORKLOAD, "cta": "cl3m_m117m_b2.0_comm2000",
+            "local": "cl500k_m8m_b2.3_clq200"}[args.profile]
+    rp, col = graphgen.workload(name)
+    rpd = torch.from_numpy(rp).to(dev)
+    cd = torch.from_numpy(col.view(np.int32)).to(dev)
+    dag = pvt.orient(rpd, cd)
+    if args.profile == "lanes":
+        C = pvt.to_ints(dag.count_global())
+        print("profile lanes: omega", max(k for k, c in enumerate(C) if c))
+    elif args.profile == "cta":
+        h = dag.count_hist(0, 20000, kmax=5)
+        print("profile cta: leaves", int(h.sum().item()))
+    elif args.profile == "local":
+        dag.count_local_vertex(kmax=12)
+        dag.count_local_edge(kmax=12)
+        print("profile local: rows", dag.n, dag.m)
+    else:
+        print("profile peel: alpha", dag.alpha)
+    torch.cuda.synchronize(dev)
+    dag.free()
+
+
 def main():
     args = parse()
     ws, rank, local = dist_setup(args)
     if args.impl == "reference":
         run_reference(args, ws, rank)
+        return
+    if args.profile:
+        import torch
+        run_profile_case(args, torch.device("cuda", local))
         return
 
     import torch

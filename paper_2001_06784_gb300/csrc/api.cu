@@ -186,6 +186,7 @@ static void dag_release(pvt_dag *g)
         release(g->qframes[c].p);
         release(g->qready[c].p);
         release(g->gstack[c].p);
+        release(g->etab[c].p);
     }
     release(g->cframes.p);
     release(g->range_roots.p);

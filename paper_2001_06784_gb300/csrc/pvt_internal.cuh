@@ -92,6 +92,7 @@ struct pvt_dag {
     cudaEvent_t ev_t0[pvt::NPHASE] = {}, ev_t1[pvt::NPHASE] = {};
     bool phase_used[pvt::NPHASE] = {};
     pvt::DevBuf<uint32_t> gstack[pvt::NCLASS];  // DFS stacks of the wide classes (global memory)
+    pvt::DevBuf<uint32_t> etab[pvt::NCLASS];    // per-warp member-pair edge ids (per-edge counts)
     bool hist_valid = false;       // hist holds the leaves of the last completed global count
 };
 

@@ -52,6 +52,8 @@ struct WarpWork {
     uint32_t adj[D * RS];        // adjacency bitset rows
     uint32_t stk_s[GSTACK ? 1 : (D + 1) * NW];  // DFS stack: S bitsets
     uint32_t *gstk;              // this warp's (D+1)*NW-word stack (GSTACK)
+    uint32_t *etab;              // per-edge counts: this warp's D x D edge ids of member pairs
+                                 // (written by the gather; null: search the out-lists)
     uint32_t hp[D + 1];          // DFS stack: (h << 16) | p
     // local counts only (point into a shared-memory region of LOCAL_BYTES):
     uint16_t *lk;                // DFS stack: link into the frame
@@ -143,6 +145,7 @@ struct CountArgs {
     uint32_t *qctl;             // counters, each on its own 128-byte line (Q_* offsets)
     unsigned qcap;              // power of two
     uint32_t *gstack;           // wide classes: per-warp DFS stacks, (32*NW+1)*NW words each
+    uint32_t *eidtab;           // per-edge counts: per-warp (32*NW)^2 edge-id tables (or null)
     // two-phase global counts: the wide walk emits every compacted subtree
     // as a frame (layout below) for k_walk_frames; null: walk them in place
     uint32_t *emit;             // [emit_cap][FRAME_WORDS]
@@ -313,6 +316,7 @@ __device__ __forceinline__ uint32_t member_edge_id(const WarpWork<NW> &Wk, const
 {
     if (a == d) return A.oeid[rbeg + b];
     if (b == d) return A.oeid[rbeg + a];
+    if (Wk.etab) return Wk.etab[a * WarpWork<NW>::D + b];
     // the edge sits in exactly one of N+(u_a), N+(u_b): search both
     for (int t = 0; t < 2; ++t) {
         int x = t ? b : a, y = t ? a : b;
@@ -388,18 +392,25 @@ __device__ void local_leaf(WarpWork<NW> &Wk, const CountArgs &A, int lane, uint3
             else add_binom_row(cell, h + 1, p - 1, A);
         }
     } else {
-        // Alg. 2 steps hht / pht / ppt over unordered member pairs
+        // Alg. 2 steps hht / pht / ppt over unordered member pairs, the
+        // L(L-1)/2 pairs (a < b) numbered row by row and dealt to the lanes
         const int L = h + p;
-        for (int a = 0; a < L - 1; ++a) {
-            for (int b = a + 1 + lane; b < L; b += 32) {
-                int la = a < h ? Wk.memH[a] : Wk.memP[a - h];
-                int lb = b < h ? Wk.memH[b] : Wk.memP[b - h];
-                uint32_t e = member_edge_id(Wk, A, rbeg, d, la, lb);
-                if (e == 0xFFFFFFFFu) continue;
-                unsigned long long *cell = A.out + (size_t)e * (A.kmax + 1) * A.W;
-                int npiv = (a >= h) + (b >= h);
-                add_binom_row(cell, h + npiv, p - npiv, A);
-            }
+        const int npairs = L * (L - 1) / 2;
+        for (int t = lane; t < npairs; t += 32) {
+            // row a of pair t: the largest a with a(2L - a - 1)/2 <= t
+            const float r2 = (float)(2 * L - 1);
+            int a = (int)((r2 - sqrtf(r2 * r2 - 8.0f * (float)t)) * 0.5f);
+            a = max(0, min(a, L - 2));
+            while (a > 0 && a * (2 * L - a - 1) / 2 > t) --a;
+            while (a + 1 <= L - 2 && (a + 1) * (2 * L - a - 2) / 2 <= t) ++a;
+            const int b = t - a * (2 * L - a - 1) / 2 + a + 1;
+            const int la = a < h ? Wk.memH[a] : Wk.memP[a - h];
+            const int lb = b < h ? Wk.memH[b] : Wk.memP[b - h];
+            const uint32_t e = member_edge_id(Wk, A, rbeg, d, la, lb);
+            if (e == 0xFFFFFFFFu) continue;
+            unsigned long long *cell = A.out + (size_t)e * (A.kmax + 1) * A.W;
+            const int npiv = (a >= h) + (b >= h);
+            add_binom_row(cell, h + npiv, p - npiv, A);
         }
     }
     __syncwarp();
@@ -710,6 +721,7 @@ __device__ void walk_root(WarpWork<NW> &Wk, unsigned long long *shist, const Cou
     for (uint32_t t0 = lane; t0 < T; t0 += 128) {
         uint32_t x[4];
         int mi[4];
+        int64_t at[4];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             const uint32_t t = t0 + 32u * q;
@@ -717,7 +729,8 @@ __device__ void walk_root(WarpWork<NW> &Wk, unsigned long long *shist, const Cou
             if (t < T) {
                 while (Wk.off[lo + 1] <= t) ++lo;  // stops by off[d] = T > t
                 mi[q] = lo;
-                x[q] = A.ocol[Wk.rs[lo] + (t - Wk.off[lo])];
+                at[q] = Wk.rs[lo] + (t - Wk.off[lo]);
+                x[q] = A.ocol[at[q]];
             }
         }
 #pragma unroll
@@ -732,6 +745,11 @@ __device__ void walk_root(WarpWork<NW> &Wk, unsigned long long *shist, const Cou
                 const int u = mi[q];
                 atomicOr(&Wk.adj[u * RS + (a >> 5)], 1u << (a & 31));
                 atomicOr(&Wk.adj[a * RS + (u >> 5)], 1u << (u & 31));
+                if (MODE == MODE_EDGE && Wk.etab) {
+                    const uint32_t e = A.oeid[at[q]];
+                    Wk.etab[u * D + a] = e;
+                    Wk.etab[a * D + u] = e;
+                }
             }
         }
     }
@@ -958,10 +976,11 @@ constexpr size_t smem_bytes()
 // shared-memory region after the histogram, global DFS stack of wide classes.
 template <int NW, int MODE>
 __device__ __forceinline__ void bind_warp(WarpWork<NW> &Wk, unsigned char *local_base, int wid, uint32_t *gstack,
-                                          unsigned warp_global)
+                                          unsigned warp_global, uint32_t *eidtab = nullptr)
 {
     if (MODE != MODE_GLOBAL) Wk.bind_local(local_base + (size_t)wid * WarpWork<NW>::LOCAL_BYTES);
     if (WarpWork<NW>::GSTACK) Wk.gstk = gstack + (size_t)warp_global * (32 * NW + 1) * NW;
+    Wk.etab = MODE == MODE_EDGE && eidtab ? eidtab + (size_t)warp_global * WarpWork<NW>::D * WarpWork<NW>::D : nullptr;
 }
 
 // Lane 0 of a split launch: the next item -- 2 with v = a fresh item index
@@ -1016,7 +1035,7 @@ __global__ void __launch_bounds__(32 * warps_per_block<NW>())
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     bind_warp<NW, MODE>(ww[wid],
                         reinterpret_cast<unsigned char *>(shist) + (SHIST ? sizeof(unsigned long long) * HIST_H * HIST_P : 0),
-                        wid, A.gstack, blockIdx.x * WPB + wid);
+                        wid, A.gstack, blockIdx.x * WPB + wid, A.eidtab);
     WalkCounters wc;
     if (SHIST) {
         for (int i = threadIdx.x; i < HIST_H * HIST_P; i += blockDim.x) shist[i] = 0;
@@ -1171,6 +1190,13 @@ pvt_status launch_class(pvt_dag *g, const CountArgs &base, int cls, cudaStream_t
             return PVT_ECUDA;
         }
         grid = std::min<unsigned>((unsigned)(g->num_sms * per_sm), need);
+    }
+    if (MODE == MODE_EDGE && persist && NW <= 8) {
+        // per-warp edge-id tables of member pairs (the gather fills them)
+        constexpr size_t D = WarpWork<NW>::D;
+        pvt_status st = grow(g->etab[cls], (size_t)grid * WPB * D * D, s);
+        if (st != PVT_OK) return st;
+        A.eidtab = g->etab[cls].p;
     }
     phase_begin(g, 1 + cls, s);
     kern<<<grid, 32 * WPB, smem, s>>>(A);
