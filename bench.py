@@ -270,14 +270,11 @@ def torch_flush(dev):
     return f
 
 
-def serving_stream(q, seed=5):
-    """Query stream: independent ER or Chung-Lu graphs, n log-uniform in
+def serving_specs(q, seed=5):
+    """Parameters of the query stream, drawn in order from one seeded
+    generator: independent ER or Chung-Lu graphs, n log-uniform in
     [100, 50000], average degree U[5, 60], exponent U[2.0, 2.5]; each asks
-    global all-k or per-edge counts with probability 1/2.  The parameters are
-    drawn in order from one seeded generator; the graphs are then generated
-    on host threads (the generator runs outside the interpreter lock)."""
-    import concurrent.futures as cf
-    from paper_2001_06784_gb300 import graphgen
+    global all-k or per-edge counts with probability 1/2."""
     rng = np.random.default_rng(seed)
     spec = []
     for i in range(q):
@@ -289,6 +286,14 @@ def serving_stream(q, seed=5):
         else:
             m = max(1, min(int(n * deg / 2), n * (n - 1) // 4))
             spec.append((i, n, "cl", m, float(rng.uniform(2.0, 2.5)), kind))
+    return spec
+
+
+def serving_graphs(spec):
+    """The graphs of a slice of the stream, generated on host threads (the
+    generator runs outside the interpreter lock)."""
+    import concurrent.futures as cf
+    from paper_2001_06784_gb300 import graphgen
 
     def make(sp):
         i, n, kind_g, a, beta, kind = sp
@@ -300,6 +305,12 @@ def serving_stream(q, seed=5):
 
     with cf.ThreadPoolExecutor(max_workers=os.cpu_count() or 4) as ex:
         return list(ex.map(make, spec))
+
+
+def serving_stream(q, seed=5):
+    """The whole stream of q queries (small q only: every graph stays in
+    host memory)."""
+    return serving_graphs(serving_specs(q, seed))
 
 
 def run_local(args, dev, flush):
@@ -366,6 +377,253 @@ def run_local(args, dev, flush):
         res[kind]["distribution"] = dist
         del out, t
     return res
+
+
+def run_cl3m(args, dev):
+    """All-k global counts of the com-orkut-shaped graph (Chung-Lu n = 3M,
+    m ~ 128M, exponent 2.0, 2,000 planted communities of 50-120 vertices at
+    density 0.8; degeneracy 733): one orient + count_global on the graph
+    already in HBM, timed with CUDA events, phases with the classes run one
+    after another.  Its tree holds about 1.1e12 nodes, so a count takes on
+    the order of 100 s: it is timed once, not K + W times.  Checks: C_1 = n,
+    C_2 = m and C_3 = the oracle's triangle enumeration (plain definition,
+    no SCT), word for word; every count is exact by construction (the
+    device's root-path check ran)."""
+    import torch
+    import paper_2001_06784_gb300 as pvt
+    from paper_2001_06784_gb300 import graphgen
+    import oracle
+    name = "cl3m_m117m_b2.0_comm2000"
+    rp, col = graphgen.workload(name)
+    n, m = len(rp) - 1, len(col) // 2
+    rpd = torch.from_numpy(rp).to(dev)
+    cd = torch.from_numpy(col.view(np.int32)).to(dev)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch_flush(dev)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    sampler = ClockSampler(int(str(dev).split(":")[-1]) if ":" in str(dev) else 0)
+    sampler.start()
+    e0.record(stream)
+    dag = pvt.orient(rpd, cd, profile=True)
+    so = dag.stats()
+    dag.set_policy(serial=True)
+    C = dag.count_global()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1)
+    st = dag.stats()
+    words = pvt.to_ints(C)
+    depths = dag.leaf_depths()
+    dag.free()
+    del flush
+    omega = max(k for k, c in enumerate(words) if c)
+    T = oracle.triangles(rp, col, threads=os.cpu_count() or 1)
+    ph = dict(st["ms"])
+    ph["peel"], ph["orient"] = so["ms"]["peel"], so["ms"]["orient"]
+    try:
+        alu = pvt.measure_popc_rate(dev) / 1e9
+    except Exception:
+        alu = POPC_PER_CLK_PER_SM * SM_COUNT * SM_MAX_MHZ * 1e6 / 1e9
+    names = pvt.Dag.PHASES
+    kern = []
+    for c in range(1, 7):
+        t = ph[names[1 + c]]
+        if t > 0:
+            a = st["class_words"][c] / (t / 1000.0) / 1e9
+            kern.append({"kernel": names[1 + c], "ms": t, "algorithmic": st["class_words"][c], "achieved": a,
+                         "unit": "Gop/s", "frac": a / alu, "roots": st["roots"][c]})
+    dom = max(kern, key=lambda k: k["ms"])
+    return {"workload": name, "n": n, "m": m, "alpha": len(depths) - 2, "omega": omega, "kmax": len(words) - 1,
+            "ms": ms, "edges_per_s": m / (ms / 1000.0), "counts": {"C1": words[1], "C2": words[2], "C3": words[3],
+                                                                  "C_max": str(max(words))},
+            "checks": {"C1_is_n": words[1] == n, "C2_is_m": words[2] == m, "C3_is_oracle_triangles": words[3] == T},
+            "sct": {"nodes": st["sct_nodes"], "leaves": st["sct_leaves"], "pivot_words": st["pivot_words"],
+                    "leaf_depth_mode": int(np.argmax(depths))},
+            "phases_ms": ph, "kernels": kern,
+            "roofline": {"bound": "alu", "kernel": dom["kernel"], "achieved": dom["achieved"], "peak": alu,
+                         "unit": "Gop/s", "frac": dom["frac"]},
+            "clocks": clocks,
+            "timing": "one orient + all-k count, CUDA events, classes serialised (policy.serial)"}
+
+
+def run_graph_replay(args, dev, reps=50):
+    """Global counts on a resident small graph (ER n=2000, avg degree 20,
+    one 30-clique), called repeatedly: the launch sequence issued directly
+    against the replay of its recorded CUDA graph (device time per call,
+    CUDA events around each call)."""
+    import torch
+    import paper_2001_06784_gb300 as pvt
+    from paper_2001_06784_gb300 import graphgen
+    name = "er2k_d20_clique30"
+    rp, col = graphgen.workload(name)
+    dag = pvt.orient(torch.from_numpy(rp).to(dev), torch.from_numpy(col.view(np.int32)).to(dev))
+    stream = torch.cuda.current_stream(dev)
+    out = torch.empty((dag.alpha + 2, dag.min_words), dtype=torch.int64, device=dev)
+    res = {"workload": name}
+    ref = None
+    for form in ("direct", "graph"):
+        dag.set_policy(graph=(form == "graph"))
+        ms = []
+        for i in range(reps + 3):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            t0 = time.perf_counter()
+            e0.record(stream)
+            dag.count_global(out=out)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            if i >= 3:
+                ms.append((e0.elapsed_time(e1), (time.perf_counter() - t0) * 1000.0))
+        got = pvt.to_ints(out)
+        ref = got if ref is None else ref
+        assert got == ref, "graph replay differs from direct launches"
+        res[form] = {"device_ms": float(np.median([a for a, _ in ms])),
+                     "host_ms": float(np.median([b for _, b in ms])), "launches": dag.stats()["launches"]}
+    dag.free()
+    return res
+
+
+SERVING_CHUNK = 2000  # queries held in host memory at once (about 2 GB of CSR)
+
+
+def run_serving(args, dev):
+    """The query server (continuous batching, large queries on the whole-GPU
+    direct path beside the batches) against one launch sequence per graph, on
+    the same query stream, in chunks of SERVING_CHUNK queries (the whole
+    stream's CSRs do not fit in host memory).  Per chunk: closed-loop
+    saturation throughput of each form (one query after another / every
+    query submitted at once), then p50/p99 latency with Poisson arrivals at
+    0.8 x the plain form's saturation rate (measured on the first chunk).
+    Every served result is checked word for word against the plain form's
+    (SHA-1 of the words), and the eight smallest queries of the first chunk
+    against the oracle."""
+    import hashlib
+    import threading as th
+    import torch
+    import paper_2001_06784_gb300 as pvt
+    import oracle
+    specs = serving_specs(args.serving_queries)
+    cfg = dict(mem_budget=64 << 30, max_inflight=4096, max_batch=256, streams=4)
+
+    def digest(a):
+        return hashlib.sha1(np.ascontiguousarray(a).view(np.uint8)).hexdigest()
+
+    def plain_one(rp, col, kind):
+        rpd = torch.from_numpy(rp).to(dev, non_blocking=True)
+        cd = torch.from_numpy(col.view(np.int32)).to(dev, non_blocking=True)
+        dag = pvt.orient(rpd, cd)
+        out = dag.count_global() if kind == "global" else dag.count_local_edge()
+        host = out.cpu().numpy().view(np.uint64)
+        dag.free()
+        return host.reshape((1,) + host.shape) if kind == "global" else host
+
+    lam = None
+    edges = 0
+    t_sat_plain = t_sat_srv = 0.0
+    lat_plain, lat_srv = [], []
+    span_plain = span_srv = 0.0
+    mismatch = 0
+    oracle_ok, n_oracle = True, 0
+    for c0 in range(0, len(specs), SERVING_CHUNK):
+        qs = serving_graphs(specs[c0:c0 + SERVING_CHUNK])
+        edges += sum(len(c) // 2 for _, c, _ in qs)
+        if c0 == 0:
+            for rp, col, kind in qs[:3]:  # warm-up
+                plain_one(rp, col, kind)
+            torch.cuda.synchronize(dev)
+        # ---- closed loop, plain: one query after another
+        plain_hash = []
+        t0 = time.perf_counter()
+        for rp, col, kind in qs:
+            plain_hash.append(digest(plain_one(rp, col, kind)))
+        dt = time.perf_counter() - t0
+        t_sat_plain += dt
+        if lam is None:
+            lam = 0.8 * len(qs) / dt
+        arrivals = np.cumsum(np.random.default_rng(55 + c0).exponential(1.0 / lam, len(qs)))
+        small = sorted(range(len(qs)), key=lambda i: len(qs[i][1]))[:8] if c0 == 0 else []
+        kept = {}
+        with pvt.Server(**cfg) as sv:
+            for rp, col, kind in qs[:3]:  # warm-up
+                t = sv.submit(rp, col, kind)
+                sv.wait(t)
+                sv.result(t)
+            # ---- closed loop, served: every query submitted at once
+            t0 = time.perf_counter()
+            tickets = [sv.submit(rp, col, kind) for rp, col, kind in qs]
+            for i, t in enumerate(tickets):
+                sv.wait(t)
+                words, _ = sv.result(t)
+                mismatch += digest(words) != plain_hash[i]
+                if i in small:
+                    kept[i] = words
+            t_sat_srv += time.perf_counter() - t0
+        for i in small:
+            rp, col, kind = qs[i]
+            K = kept[i].shape[1] - 1
+            ref = oracle.count(rp, col, kmax=K, edge=kind == "edge")
+            want = ref["C"] if kind == "global" else oracle.to_int(ref["ce"])
+            got = pvt.to_ints(kept[i][0]) if kind == "global" else pvt.to_ints(kept[i])
+            oracle_ok = oracle_ok and got == want
+            n_oracle += 1
+        # ---- open loop, plain: replayed in real time, one query at a time
+        t0 = time.perf_counter()
+        for (rp, col, kind), ta in zip(qs, arrivals):
+            now = time.perf_counter() - t0
+            if now < ta:
+                time.sleep(ta - now)
+            plain_one(rp, col, kind)
+            lat_plain.append(time.perf_counter() - t0 - ta)
+        span_plain += time.perf_counter() - t0
+        # ---- open loop, served: a submitter thread keeps the arrivals,
+        # latency measured inside the server (submit -> result ready)
+        lat = [None] * len(qs)
+        with pvt.Server(**cfg) as sv:
+            for rp, col, kind in qs[:3]:  # warm-up
+                t = sv.submit(rp, col, kind)
+                sv.wait(t)
+                sv.result(t)
+            tickets = [None] * len(qs)
+            t0 = time.perf_counter()
+
+            def submitter():
+                for i, ((rp, col, kind), ta) in enumerate(zip(qs, arrivals)):
+                    now = time.perf_counter() - t0
+                    if now < ta:
+                        time.sleep(ta - now)
+                    tickets[i] = sv.submit(rp, col, kind)
+
+            thr = th.Thread(target=submitter)
+            thr.start()
+            for i in range(len(qs)):
+                while tickets[i] is None:
+                    time.sleep(0.0005)
+                sv.wait(tickets[i])
+                _, lat[i] = sv.result(tickets[i])
+            thr.join()
+            span_srv += time.perf_counter() - t0
+        lat_srv += lat
+        del qs
+
+    def summary(lat, span):
+        a = np.asarray(lat) * 1000.0
+        return {"p50_ms": float(np.percentile(a, 50)), "p99_ms": float(np.percentile(a, 99)),
+                "mean_ms": float(a.mean()), "throughput_qps": len(a) / span, "edges_per_s": edges / span}
+
+    nq = len(specs)
+    return {"queries": nq, "chunk": SERVING_CHUNK,
+            "stream": "ER or Chung-Lu, n log-uniform 100..50000, avg deg U[5,60], "
+                      "global or per-edge (1/2 each), Poisson arrivals, seed 5",
+            "edges_total": edges,
+            "saturation": {"plain_qps": nq / t_sat_plain, "served_qps": nq / t_sat_srv,
+                           "plain_edges_per_s": edges / t_sat_plain, "served_edges_per_s": edges / t_sat_srv,
+                           "form": "closed loop: plain one query after another; served all of a chunk at once"},
+            "arrival_rate_qps": lam,
+            "plain": summary(lat_plain, span_plain), "batched": summary(lat_srv, span_srv),
+            "check": {"served_vs_plain_mismatches": int(mismatch), "oracle_sample": n_oracle,
+                      "oracle_sample_ok": bool(oracle_ok)}}
 
 
 def run_cl3m(args, dev):
@@ -784,22 +1042,30 @@ def main():
                    "frame_words": walk["frame_words"], "frames": walk["frames"]},
            "peel": {"rounds": so["peel_rounds"], "levels": so["peel_levels"]}}
 
+    def section(key, fn):
+        """A secondary measurement; its failure is reported in its place
+        instead of losing the line."""
+        try:
+            out[key] = fn()
+        except Exception as exc:  # noqa: BLE001 - reported in the JSON line
+            out[key] = {"error": f"{type(exc).__name__}: {exc}"}
+
     # ---- launch cost: direct launches vs replay of the recorded CUDA graph
     if rank == 0:
-        out["graph_replay"] = run_graph_replay(args, dev)
+        section("graph_replay", lambda: run_graph_replay(args, dev))
 
     # ---- local counts (per-vertex, per-edge) on the 500k-vertex graph
     if rank == 0 and not args.no_local:
-        out["local"] = run_local(args, dev, flush)
+        section("local", lambda: run_local(args, dev, flush))
+    del flush
 
     # ---- all-k counts of the 128M-edge com-orkut-shaped graph, timed once
     if rank == 0 and not args.no_cl3m:
-        del flush
-        out["cl3m_allk"] = run_cl3m(args, dev)
+        section("cl3m_allk", lambda: run_cl3m(args, dev))
 
     # ---- serving: Poisson stream of independent queries (rank 0 only)
     if rank == 0 and args.serving_queries > 0:
-        out["serving"] = run_serving(args, dev)
+        section("serving", lambda: run_serving(args, dev))
 
     # ---- CPU baseline: the oracle, whole workload, every host core (the
     # paper's parallel scheme) and one core (its sequential form); also
