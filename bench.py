@@ -861,15 +861,15 @@ def run_serving(args, dev):
 def run_profile_case(args, dev):
     """One small case per kernel family, for ncu (`--profile`):
     lanes  orient + global count of the bench graph (the frame phase, k_lanes)
-    cta    orient the 128M-edge graph, then the roots with ids below 20,000
-           (a range that holds heavy roots), kmax = 5 (k_cta)
+    cta    orient the bench graph, global count k <= 4 with the 129..256
+           out-degree class on the block-per-root kernel (k_cta<8>)
     local  per-vertex and per-edge tables of the 500k-vertex graph, k <= 12
            (k_count in MODE_VERTEX / MODE_EDGE)
     peel   orient the bench graph (k_peel, k_peel_tail)"""
     import torch
     import paper_2001_06784_gb300 as pvt
     from paper_2001_06784_gb300 import graphgen
-    name = {"lanes": DEFAULT_WORKLOAD, "peel": DEFAULT_WORKLOAD, "cta": "cl3m_m117m_b2.0_comm2000",
+    name = {"lanes": DEFAULT_WORKLOAD, "peel": DEFAULT_WORKLOAD, "cta": DEFAULT_WORKLOAD,
             "local": "cl500k_m8m_b2.3_clq200"}[args.profile]
     rp, col = graphgen.workload(name)
     rpd = torch.from_numpy(rp).to(dev)
@@ -879,8 +879,9 @@ def run_profile_case(args, dev):
         C = pvt.to_ints(dag.count_global())
         print("profile lanes: omega", max(k for k, c in enumerate(C) if c))
     elif args.profile == "cta":
-        h = dag.count_hist(0, 20000, kmax=5)
-        print("profile cta: leaves", int(h.sum().item()))
+        dag.set_policy(cta=[0, 0, 0, 0, 1, 0, 0])
+        C = pvt.to_ints(dag.count_global(kmax=4))
+        print("profile cta: C4", C[4])
     elif args.profile == "local":
         dag.count_local_vertex(kmax=12)
         dag.count_local_edge(kmax=12)

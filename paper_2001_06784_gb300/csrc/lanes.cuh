@@ -32,6 +32,7 @@ namespace pvt {
 constexpr int LANE_WPB = 8;     // warps per block
 constexpr int LSTK = 32;        // per-lane stack slots (a label of s <= 32 keeps at most 31 pending)
 constexpr unsigned LANE_DONATE_EVERY = 32;  // node steps between looks at the ring queue
+constexpr unsigned LANE_DONATE_MAX = 4;     // entries one look may donate
 
 struct LaneWork {
     uint32_t rows[32][32];      // rows[v][lane]: row v of the lane's current subtree
@@ -332,31 +333,30 @@ __device__ inline void lane_walk(LaneWork &L, unsigned *sh32, const CountArgs &A
         if (has) lane_node(L, sh32, A, lane, S, h, p, has, top, bot, lc);
         __syncwarp();
         if (++steps % LANE_DONATE_EVERY == 0) {
-            // a warp waits on the ring: donate the oldest pending entry of the
-            // lane with the most pending entries, with that lane's rows
-            int hungry = lane == 0 ? (int)queue_hungry(A) : 0;
-            hungry = __shfl_sync(FULL, hungry, 0);
-            if (hungry) {
+            // warps wait on the ring: donate, for up to LANE_DONATE_MAX of
+            // them, the oldest pending entry of the lane with the most pending
+            // entries, with that lane's rows
+            unsigned waiters = lane == 0 ? queue_waiters(A, LANE_DONATE_MAX) : 0u;
+            waiters = __shfl_sync(FULL, waiters, 0);
+            for (unsigned d = 0; d < waiters; ++d) {
                 const unsigned pend = top - bot;
                 const unsigned key =
                     pend >= 2 && __popc(L.stkS[bot & (LSTK - 1)][lane]) >= DONATE_MIN_COMPACT ? (pend << 5) | (unsigned)lane : 0u;
                 const unsigned best = __reduce_max_sync(FULL, key);
-                if (best) {
-                    const int dl = (int)(best & 31u);
-                    unsigned t = 0;
-                    uint32_t *fr = frame_reserve(A, lane, t);
-                    if (fr) {
-                        fr[4 + lane] = L.rows[lane][dl];
-                        if (lane == dl) {
-                            fr[0] = FRAME_COMPACT;
-                            fr[1] = L.stkHP[bot & (LSTK - 1)][lane];
-                            fr[2] = L.stkS[bot & (LSTK - 1)][lane];
-                            fr[3] = (uint32_t)A.cls;
-                            ++bot;
-                        }
-                        frame_publish(A, lane, t);
-                    }
+                if (!best) break;
+                const int dl = (int)(best & 31u);
+                unsigned t = 0;
+                uint32_t *fr = frame_reserve(A, lane, t);
+                if (!fr) break;
+                fr[4 + lane] = L.rows[lane][dl];
+                if (lane == dl) {
+                    fr[0] = FRAME_COMPACT;
+                    fr[1] = L.stkHP[bot & (LSTK - 1)][lane];
+                    fr[2] = L.stkS[bot & (LSTK - 1)][lane];
+                    fr[3] = (uint32_t)A.cls;
+                    ++bot;
                 }
+                frame_publish(A, lane, t);
             }
         }
     }

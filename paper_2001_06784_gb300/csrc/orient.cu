@@ -86,13 +86,33 @@ struct PeelState {
 // in shared memory, and a level costs block barriers instead of grid ones.
 constexpr unsigned TAIL_MAX = 16384;
 constexpr int TAIL_THREADS = 1024;
+// residual-row entries a lane loads before it uses the first
+constexpr int TAIL_UNROLL = 8;
 
 constexpr unsigned long long BARRIER_LIMIT_NS = 4000000000ull;  // 4 s
 constexpr unsigned long long CASCADE_LIMIT_NS = 4000000000ull;  // 4 s without progress
 constexpr uint32_t EMPTY = 0xFFFFFFFFu;
+// a removal-queue entry whose vertex the pushing warp processes itself
+// (vertex ids stop at 0xFFFFFFFD)
+constexpr uint32_t TAKEN = 0xFFFFFFFEu;
 // bulk processing of a level's scan pushes: from this many pushes on, one
 // thread per pushed vertex, for out-lists up to BULK_LANE_MAX entries
 constexpr unsigned BULK_MIN = 4096, BULK_LANE_MAX = 64;
+
+// Rows are read PEEL_UNROLL entries per lane at a time: every load, then
+// every degree decrement, is in flight before the first result is used.
+constexpr int PEEL_UNROLL = 4;
+
+// One removal found by a decrement (bulk phase: single pushes, no warp
+// aggregation).
+__device__ __forceinline__ void peel_push_one(PeelState *st, uint32_t *rnd, uint32_t *core, uint32_t *lq,
+                                              uint32_t u, unsigned k)
+{
+    const unsigned pos = atomicAdd(&st->tail, 1u);
+    rnd[u] = pos;
+    core[u] = k;
+    *(volatile uint32_t *)(lq + pos) = u;
+}
 
 // Grid-wide barrier for a cooperative launch, with a bounded wait: on
 // timeout it sets DERR_TIMEOUT and every block leaves the kernel.
@@ -144,8 +164,12 @@ __device__ bool grid_barrier(PeelState *st, unsigned *err)
 //            degree is <= k, else appended to the next alive list;
 //   cascade  warps take queue entries one at a time and lower the residual
 //            degree of every neighbour of the entry; the one decrement that
-//            takes a neighbour from k+1 to k pushes it at once.  The level
-//            ends when every pushed entry has been processed (done == tail).
+//            takes a neighbour from k+1 to k pushes it at once.  A warp
+//            processes the first vertex its own decrements push (its queue
+//            entry is marked taken) before it claims another entry: a chain
+//            of pushes then skips the queue's publish/claim round trip.  The
+//            level ends when every pushed entry has been processed
+//            (done == tail).
 // Every vertex is pushed exactly once, so its queue position is a unique
 // removal time: rnd[v].  Neighbours already removed are decremented too: a
 // removed vertex's degree is <= k and only falls, so it can never be pushed
@@ -271,32 +295,36 @@ __global__ void __launch_bounds__(1024, 1) k_peel(int64_t n, const int64_t *__re
                 }
                 const bool mine = e - b <= (int64_t)BULK_LANE_MAX;
                 if (mine) {
-                    for (int64_t j = b; j < e; ++j) {
-                        const uint32_t u = col[j];
-                        const unsigned old = atomicSub(&deg[u], 1u);
-                        if (old == k + 1) {
-                            const unsigned pos = atomicAdd(&st->tail, 1u);
-                            rnd[u] = pos;
-                            core[u] = k;
-                            *(volatile uint32_t *)(lq + pos) = u;
-                        } else if (old > k + 1) {
-                            mnext = min(mnext, old - 1);
+                    for (int64_t j = b; j < e; j += PEEL_UNROLL) {
+                        uint32_t u[PEEL_UNROLL];
+                        unsigned old[PEEL_UNROLL];
+#pragma unroll
+                        for (int t = 0; t < PEEL_UNROLL; ++t) u[t] = j + t < e ? col[j + t] : EMPTY;
+#pragma unroll
+                        for (int t = 0; t < PEEL_UNROLL; ++t) old[t] = u[t] != EMPTY ? atomicSub(&deg[u[t]], 1u) : 0u;
+#pragma unroll
+                        for (int t = 0; t < PEEL_UNROLL; ++t) {
+                            if (u[t] == EMPTY) continue;
+                            if (old[t] == k + 1) peel_push_one(st, rnd, core, lq, u[t], k);
+                            else if (old[t] > k + 1) mnext = min(mnext, old[t] - 1);
                         }
                     }
                 }
                 for (unsigned big = __ballot_sync(FULL, !mine); big; big &= big - 1) {
                     const int src = __ffs(big) - 1;
                     const int64_t bb = __shfl_sync(FULL, b, src), ee = __shfl_sync(FULL, e, src);
-                    for (int64_t j = bb + lane; j < ee; j += 32) {
-                        const uint32_t u = col[j];
-                        const unsigned old = atomicSub(&deg[u], 1u);
-                        if (old == k + 1) {
-                            const unsigned pos = atomicAdd(&st->tail, 1u);
-                            rnd[u] = pos;
-                            core[u] = k;
-                            *(volatile uint32_t *)(lq + pos) = u;
-                        } else if (old > k + 1) {
-                            mnext = min(mnext, old - 1);
+                    for (int64_t j0 = bb + lane; j0 < ee; j0 += 32 * PEEL_UNROLL) {
+                        uint32_t u[PEEL_UNROLL];
+                        unsigned old[PEEL_UNROLL];
+#pragma unroll
+                        for (int t = 0; t < PEEL_UNROLL; ++t) u[t] = j0 + 32 * t < ee ? col[j0 + 32 * t] : EMPTY;
+#pragma unroll
+                        for (int t = 0; t < PEEL_UNROLL; ++t) old[t] = u[t] != EMPTY ? atomicSub(&deg[u[t]], 1u) : 0u;
+#pragma unroll
+                        for (int t = 0; t < PEEL_UNROLL; ++t) {
+                            if (u[t] == EMPTY) continue;
+                            if (old[t] == k + 1) peel_push_one(st, rnd, core, lq, u[t], k);
+                            else if (old[t] > k + 1) mnext = min(mnext, old[t] - 1);
                         }
                     }
                 }
@@ -312,54 +340,99 @@ __global__ void __launch_bounds__(1024, 1) k_peel(int64_t n, const int64_t *__re
         const unsigned want = min(max(waiting > (1u << 28) ? (1u << 30) : 4u * waiting, 256u), (unsigned)(nthreads >> 5));
         const unsigned per_block = (want + gridDim.x - 1) / gridDim.x;
         if ((unsigned)wid < per_block) {
+            const unsigned below = (1u << lane) - 1u;
             unsigned claim = EMPTY;  // lane 0: this warp's queue position
+            unsigned ndone = 0;      // lane 0: entries processed and not yet counted in done
+            // a vertex this warp pushed and processes itself (warp-uniform),
+            // with its row bounds already loaded
+            uint32_t keep = EMPTY;
+            int64_t kb = 0, ke = 0;
             for (;;) {
-                int got = 0;  // 1: vertex in `v`, 2: level done, 3: error
-                uint32_t v = 0;
-                if (lane == 0) {
-                    if (claim == EMPTY) claim = atomicAdd(&st->head, 1u) + (bulk ? se - t_start : 0u);
-                    unsigned spins = 0, last = 0xFFFFFFFFu;
-                    unsigned long long t0 = 0;
-                    for (;;) {
-                        if (claim < (uint64_t)n) {
-                            const uint32_t x = *(volatile uint32_t *)(lq + claim);
-                            if (x != EMPTY) { v = x; got = 1; break; }
+                int64_t b = kb, e = ke;
+                if (keep == EMPTY) {
+                    int got = 0;  // 1: vertex in `v`, 2: level done, 3: error
+                    uint32_t v = 0;
+                    if (lane == 0) {
+                        // report the finished entries before waiting: the level
+                        // cannot end while they are uncounted
+                        if (ndone) {
+                            __threadfence();  // their pushes are counted before they are done
+                            atomicAdd(&st->done, ndone);
+                            ndone = 0;
                         }
-                        if ((++spins & 7u) == 0) {
-                            // quiescent once every pushed entry is processed; read
-                            // done before tail (done <= tail at all times)
-                            const unsigned dn = vst->done;
-                            __threadfence();
-                            if (vst->tail == dn) { got = 2; break; }
-                            if (*(volatile unsigned *)err & DERR_TIMEOUT) { got = 3; break; }
-                            if (dn != last) { last = dn; t0 = global_ns(); }
-                            else if (global_ns() - t0 > CASCADE_LIMIT_NS) { atomicOr(err, DERR_TIMEOUT); got = 3; break; }
+                        unsigned spins = 0, last = 0xFFFFFFFFu;
+                        unsigned long long t0 = 0;
+                        for (;;) {
+                            if (claim == EMPTY) claim = atomicAdd(&st->head, 1u) + (bulk ? se - t_start : 0u);
+                            if (claim < (uint64_t)n) {
+                                const uint32_t x = *(volatile uint32_t *)(lq + claim);
+                                if (x == TAKEN) { claim = EMPTY; continue; }  // its pusher processes it
+                                if (x != EMPTY) { v = x; got = 1; break; }
+                            }
+                            if ((++spins & 7u) == 0) {
+                                // quiescent once every pushed entry is processed; read
+                                // done before tail (done <= tail at all times)
+                                const unsigned dn = vst->done;
+                                __threadfence();
+                                if (vst->tail == dn) { got = 2; break; }
+                                if (*(volatile unsigned *)err & DERR_TIMEOUT) { got = 3; break; }
+                                if (dn != last) { last = dn; t0 = global_ns(); }
+                                else if (global_ns() - t0 > CASCADE_LIMIT_NS) { atomicOr(err, DERR_TIMEOUT); got = 3; break; }
+                            }
+                            __nanosleep(spins < 64 ? 20 : 200);
                         }
-                        __nanosleep(spins < 64 ? 20 : 200);
+                        if (got == 1) claim = EMPTY;
                     }
-                    if (got == 1) claim = EMPTY;
+                    got = __shfl_sync(FULL, got, 0);
+                    if (got == 3) return;
+                    if (got == 2) break;
+                    v = __shfl_sync(FULL, v, 0);
+                    b = rp[v];
+                    e = rp[v + 1];
                 }
-                got = __shfl_sync(FULL, got, 0);
-                if (got == 3) return;
-                if (got == 2) break;
-                v = __shfl_sync(FULL, v, 0);
-                for (int64_t j = rp[v] + lane; j < rp[v + 1]; j += 32) {
-                    const uint32_t u = col[j];
-                    const unsigned old = atomicSub(&deg[u], 1u);
-                    if (old == k + 1) {
-                        const unsigned pos = atomicAdd(&st->tail, 1u);
-                        rnd[u] = pos;
-                        core[u] = k;
-                        *(volatile uint32_t *)(lq + pos) = u;
-                    } else if (old > k + 1) {
-                        mnext = min(mnext, old - 1);
+                keep = EMPTY;
+                // lower the neighbours' degrees; the pushes of one
+                // 32 * PEEL_UNROLL-entry stretch take consecutive queue
+                // positions (one atomic), and the warp keeps the first of them
+                // when it holds none
+                for (int64_t j0 = b + lane; __any_sync(FULL, j0 < e); j0 += 32 * PEEL_UNROLL) {
+                    uint32_t u[PEEL_UNROLL];
+                    unsigned old[PEEL_UNROLL], bp[PEEL_UNROLL];
+#pragma unroll
+                    for (int t = 0; t < PEEL_UNROLL; ++t) u[t] = j0 + 32 * t < e ? col[j0 + 32 * t] : EMPTY;
+#pragma unroll
+                    for (int t = 0; t < PEEL_UNROLL; ++t) old[t] = u[t] != EMPTY ? atomicSub(&deg[u[t]], 1u) : 0u;
+                    unsigned tot = 0;
+                    uint32_t kv = EMPTY;
+#pragma unroll
+                    for (int t = 0; t < PEEL_UNROLL; ++t) {
+                        if (u[t] != EMPTY && old[t] > k + 1) mnext = min(mnext, old[t] - 1);
+                        bp[t] = __ballot_sync(FULL, u[t] != EMPTY && old[t] == k + 1);
+                        tot += __popc(bp[t]);
+                        if (kv == EMPTY && bp[t]) kv = __shfl_sync(FULL, u[t], __ffs(bp[t]) - 1);
+                    }
+                    if (!tot) continue;
+                    const bool take = keep == EMPTY;
+                    if (take) {
+                        keep = kv;
+                        kb = rp[keep];  // in flight during the atomic below
+                        ke = rp[keep + 1];
+                    }
+                    unsigned pos = 0;
+                    if (lane == 0) pos = atomicAdd(&st->tail, tot);
+                    pos = __shfl_sync(FULL, pos, 0);
+#pragma unroll
+                    for (int t = 0; t < PEEL_UNROLL; ++t) {
+                        if (bp[t] >> lane & 1u) {
+                            const unsigned p = pos + __popc(bp[t] & below);
+                            rnd[u[t]] = p;
+                            core[u[t]] = k;
+                            *(volatile uint32_t *)(lq + p) = take && u[t] == kv ? TAKEN : u[t];
+                        }
+                        pos += __popc(bp[t]);
                     }
                 }
-                __syncwarp();
-                if (lane == 0) {
-                    __threadfence();  // this entry's pushes are counted before it is done
-                    atomicAdd(&st->done, 1u);
-                }
+                if (lane == 0) ++ndone;
             }
         }
         mnext = __reduce_min_sync(FULL, mnext);
@@ -493,16 +566,15 @@ __global__ void __launch_bounds__(TAIL_THREADS, 1) k_peel_tail(const int64_t *__
     }
     __syncthreads();
     unsigned top = st->top_level, levels = 0;
-    auto push = [&](unsigned i, unsigned k) {
+    // a push touches shared memory only: the removal times and core numbers
+    // of a level go out to global memory once the level is over
+    auto push = [&](unsigned i) {
         atomicOr(&sgone[i >> 5], 1u << (i & 31));
+        const unsigned pos = atomicAdd(&s_tail, 1u);
+        vq[pos] = i;
         // the warp that takes this entry runs on this SM: bring the start of
         // the vertex's residual row into L1 for it
         asm volatile("prefetch.global.L1 [%0];" ::"l"(rcol + soff[i]));
-        const unsigned pos = atomicAdd(&s_tail, 1u);
-        rnd[tv[i]] = base + pos;
-        core[tv[i]] = k;
-        __threadfence_block();
-        vq[pos] = i;
     };
     for (unsigned level = 0;; ++level) {
         const unsigned q = level & 1u;
@@ -521,7 +593,7 @@ __global__ void __launch_bounds__(TAIL_THREADS, 1) k_peel_tail(const int64_t *__
             for (; live; live &= live - 1) {
                 const unsigned i = base + __ffs(live) - 1;
                 const unsigned d = sdeg[i];
-                if (d <= k) push(i, k);
+                if (d <= k) push(i);
                 else mnext = min(mnext, d);
             }
         }
@@ -562,11 +634,18 @@ __global__ void __launch_bounds__(TAIL_THREADS, 1) k_peel_tail(const int64_t *__
                 got = __shfl_sync(FULL, got, 0);
                 if (got != 1) break;
                 i = __shfl_sync(FULL, i, 0);
-                for (unsigned j = soff[i] + lane; j < soff[i + 1]; j += 32) {
-                    const uint32_t u = rcol[j];
-                    const unsigned old = atomicSub(&sdeg[u], 1u);
-                    if (old == k + 1) push(u, k);
-                    else if (old > k + 1) mnext = min(mnext, old - 1);
+                const unsigned e = soff[i + 1];
+                for (unsigned j0 = soff[i] + lane; j0 < e; j0 += 32 * TAIL_UNROLL) {
+                    uint32_t u[TAIL_UNROLL];
+#pragma unroll
+                    for (int t = 0; t < TAIL_UNROLL; ++t) u[t] = j0 + 32 * t < e ? rcol[j0 + 32 * t] : EMPTY;
+#pragma unroll
+                    for (int t = 0; t < TAIL_UNROLL; ++t) {
+                        if (u[t] == EMPTY) continue;
+                        const unsigned old = atomicSub(&sdeg[u[t]], 1u);
+                        if (old == k + 1) push(u[t]);
+                        else if (old > k + 1) mnext = min(mnext, old - 1);
+                    }
                 }
                 __syncwarp();
                 if (lane == 0) {
@@ -579,7 +658,13 @@ __global__ void __launch_bounds__(TAIL_THREADS, 1) k_peel_tail(const int64_t *__
         if (lane == 0 && mnext != NOT_REMOVED) atomicMin(&s_min[q ^ 1u], mnext);
         __syncthreads();
         if (s_bad) return;
-        if (s_done > t_start) top = k;
+        const unsigned t_end = s_done;
+        if (t_end > t_start) top = k;
+        for (unsigned p = t_start + threadIdx.x; p < t_end; p += blockDim.x) {
+            const uint32_t v = tv[sq[p]];
+            rnd[v] = base + p;
+            core[v] = k;
+        }
         __syncthreads();  // every thread has read s_done before the claims are reset
         if (threadIdx.x == 0) s_head = s_tail;
     }

@@ -276,6 +276,15 @@ __device__ __forceinline__ bool queue_hungry(const CountArgs &A)
     return vload64(A.qctl + Q_HEAD) > vload64(A.qctl + Q_TAIL) && !(vload(A.err) & DERR_TIMEOUT);
 }
 
+// How many warps wait on the ring for a frame not yet published (at most
+// cap; 0 after a timeout).
+__device__ __forceinline__ unsigned queue_waiters(const CountArgs &A, unsigned cap)
+{
+    const unsigned long long hd = vload64(A.qctl + Q_HEAD), tl = vload64(A.qctl + Q_TAIL);
+    if (hd <= tl || (vload(A.err) & DERR_TIMEOUT)) return 0u;
+    return (unsigned)min(hd - tl, (unsigned long long)cap);
+}
+
 // Reserve the slot of the next frame (one more outstanding item); all lanes
 // get its ticket number t.  Returns nullptr (status set) if the slot never
 // frees up.

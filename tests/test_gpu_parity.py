@@ -316,17 +316,26 @@ def test_workload_cl3m_truncated(pvt):
     lambda: graphs.complete(40), lambda: graphs.multipartite([3, 5, 7, 2]), lambda: graphs.gnp(300, 0.1, 3),
     lambda: graphgen.from_edges(5, []), lambda: graphs.disjoint_cliques([1, 2, 33, 70]),
     lambda: graphgen.workload("er2k_d20_clique30"), lambda: graphgen.workload("cl1m_m10m_b2.1_comm500"),
-    lambda: graphgen.workload("cl500k_m8m_b2.3_clq200")])
+    lambda: graphgen.workload("cl500k_m8m_b2.3_clq200"),
+    # mid-size graphs: a few grid levels, then the one-block finish
+    lambda: graphgen.generate(60000, chung_lu=(400000, 2.2), seed=11),
+    lambda: graphgen.generate(200000, er_avg_deg=9, planted=[(50, 20, 60, 0.7)], seed=12)])
 def test_core_numbers(pvt, make):
     """Core numbers of the device peel equal the oracle's (sequential bucket
     peel): they do not depend on the removal order within a level, so the
-    comparison is exact; the reported alpha is the largest of them."""
+    comparison is exact; the reported alpha is the largest of them.  The
+    orientation is a degeneracy order: every vertex has at most core(v)
+    later neighbours (Sec. 3.2), and every edge is oriented once."""
     rp, col = make()
     _, core, _ = oracle.orient(rp, col)
     dag = gpu_dag(pvt, rp, col)
     got = dag.cores().cpu().numpy().view(np.uint32)
     assert np.array_equal(got, core)
     assert dag.alpha == (int(core.max()) if len(core) else 0)
+    orow, _ = dag.out_lists()
+    outdeg = np.diff(orow.cpu().numpy())
+    assert outdeg.sum() == len(col) // 2
+    assert (outdeg <= core.astype(np.int64)).all()
     dag.free()
 
 
