@@ -35,7 +35,12 @@ SM_MAX_MHZ = 2070.0
 # kernel as it is now (summarised under profiles/, with the capture's date);
 # an entry is removed whenever its kernel changes, so that the bench line
 # reports null instead of a stale figure
-NCU_DRAM_BYTES = {}
+NCU_DRAM_BYTES = {
+    # k_lanes, the frame phase of the bench graph's all-k count (332,125,440
+    # read + 3,629,568 written), `ncu --set full` of `bench.py --profile lanes`
+    # (profiles/k_lanes_cl1m_m10m_b2.1_comm500.md)
+    "walk_frames": 335755008,
+}
 
 
 def parse():
@@ -496,11 +501,11 @@ def run_serving(args, dev):
     saturation throughput of each form (one query after another / every
     query submitted at once), then p50/p99 latency with Poisson arrivals at
     0.8 x the plain form's saturation rate (measured on the first chunk).
-    Every served result is checked word for word against the plain form's
-    (SHA-1 of the words), and the eight smallest queries of the first chunk
-    against the oracle."""
-    import hashlib
+    Every served result is checked against the plain form's (length, 64-bit
+    sum and xor of the words), and the eight smallest queries of the first
+    chunk word for word against the oracle."""
     import threading as th
+    from concurrent.futures import ThreadPoolExecutor
     import torch
     import paper_2001_06784_gb300 as pvt
     import oracle
@@ -508,7 +513,10 @@ def run_serving(args, dev):
     cfg = dict(mem_budget=64 << 30, max_inflight=4096, max_batch=256, streams=4)
 
     def digest(a):
-        return hashlib.sha1(np.ascontiguousarray(a).view(np.uint8)).hexdigest()
+        # a 64-bit sum and xor of the result's words (a full hash of the
+        # 10-20 MB per-edge tables would cost more than serving them)
+        w = np.ascontiguousarray(a).reshape(-1).view(np.uint64)
+        return (w.size, int(np.add.reduce(w, dtype=np.uint64)), int(np.bitwise_xor.reduce(w)) if w.size else 0)
 
     def plain_one(rp, col, kind):
         rpd = torch.from_numpy(rp).to(dev, non_blocking=True)
@@ -533,12 +541,15 @@ def run_serving(args, dev):
             for rp, col, kind in qs[:3]:  # warm-up
                 plain_one(rp, col, kind)
             torch.cuda.synchronize(dev)
-        # ---- closed loop, plain: one query after another
+        # ---- closed loop, plain: one query after another (the checksum of
+        # each result is taken with the clock stopped)
         plain_hash = []
-        t0 = time.perf_counter()
+        dt = 0.0
         for rp, col, kind in qs:
-            plain_hash.append(digest(plain_one(rp, col, kind)))
-        dt = time.perf_counter() - t0
+            t0 = time.perf_counter()
+            res = plain_one(rp, col, kind)
+            dt += time.perf_counter() - t0
+            plain_hash.append(digest(res))
         t_sat_plain += dt
         if lam is None:
             lam = 0.8 * len(qs) / dt
@@ -550,16 +561,20 @@ def run_serving(args, dev):
                 t = sv.submit(rp, col, kind)
                 sv.wait(t)
                 sv.result(t)
-            # ---- closed loop, served: every query submitted at once
-            t0 = time.perf_counter()
-            tickets = [sv.submit(rp, col, kind) for rp, col, kind in qs]
-            for i, t in enumerate(tickets):
-                sv.wait(t)
-                words, _ = sv.result(t)
-                mismatch += digest(words) != plain_hash[i]
-                if i in small:
-                    kept[i] = words
-            t_sat_srv += time.perf_counter() - t0
+            # ---- closed loop, served: every query submitted at once (the
+            # checksums are taken by helper threads beside the loop)
+            with ThreadPoolExecutor(4) as ex:
+                t0 = time.perf_counter()
+                tickets = [sv.submit(rp, col, kind) for rp, col, kind in qs]
+                sums = []
+                for i, t in enumerate(tickets):
+                    sv.wait(t)
+                    words, _ = sv.result(t)
+                    sums.append(ex.submit(digest, words))
+                    if i in small:
+                        kept[i] = words
+                t_sat_srv += time.perf_counter() - t0
+                mismatch += sum(f.result() != plain_hash[i] for i, f in enumerate(sums))
         for i in small:
             rp, col, kind = qs[i]
             K = kept[i].shape[1] - 1
@@ -623,238 +638,6 @@ def run_serving(args, dev):
             "arrival_rate_qps": lam,
             "plain": summary(lat_plain, span_plain), "batched": summary(lat_srv, span_srv),
             "check": {"served_vs_plain_mismatches": int(mismatch), "oracle_sample": n_oracle,
-                      "oracle_sample_ok": bool(oracle_ok)}}
-
-
-def run_cl3m(args, dev):
-    """All-k global counts of the com-orkut-shaped graph (Chung-Lu n = 3M,
-    m ~ 128M, exponent 2.0, 2,000 planted communities of 50-120 vertices at
-    density 0.8; degeneracy 733): one orient + count_global on the graph
-    already in HBM, timed with CUDA events, phases with the classes run one
-    after another.  Its tree holds about 1.1e12 nodes, so a count takes on
-    the order of 100 s: it is timed once, not K + W times.  Checks: C_1 = n,
-    C_2 = m and C_3 = the oracle's triangle enumeration (plain definition,
-    no SCT), word for word; every count is exact by construction (the
-    device's root-path check ran)."""
-    import torch
-    import paper_2001_06784_gb300 as pvt
-    from paper_2001_06784_gb300 import graphgen
-    import oracle
-    name = "cl3m_m117m_b2.0_comm2000"
-    rp, col = graphgen.workload(name)
-    n, m = len(rp) - 1, len(col) // 2
-    rpd = torch.from_numpy(rp).to(dev)
-    cd = torch.from_numpy(col.view(np.int32)).to(dev)
-    stream = torch.cuda.current_stream(dev)
-    flush = torch_flush(dev)
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    sampler = ClockSampler(int(str(dev).split(":")[-1]) if ":" in str(dev) else 0)
-    sampler.start()
-    e0.record(stream)
-    dag = pvt.orient(rpd, cd, profile=True)
-    so = dag.stats()
-    dag.set_policy(serial=True)
-    C = dag.count_global()
-    e1.record(stream)
-    torch.cuda.synchronize(dev)
-    clocks = sampler.stop()
-    ms = e0.elapsed_time(e1)
-    st = dag.stats()
-    words = pvt.to_ints(C)
-    depths = dag.leaf_depths()
-    dag.free()
-    del flush
-    omega = max(k for k, c in enumerate(words) if c)
-    T = oracle.triangles(rp, col, threads=os.cpu_count() or 1)
-    ph = dict(st["ms"])
-    ph["peel"], ph["orient"] = so["ms"]["peel"], so["ms"]["orient"]
-    try:
-        alu = pvt.measure_popc_rate(dev) / 1e9
-    except Exception:
-        alu = POPC_PER_CLK_PER_SM * SM_COUNT * SM_MAX_MHZ * 1e6 / 1e9
-    names = pvt.Dag.PHASES
-    kern = []
-    for c in range(1, 7):
-        t = ph[names[1 + c]]
-        if t > 0:
-            a = st["class_words"][c] / (t / 1000.0) / 1e9
-            kern.append({"kernel": names[1 + c], "ms": t, "algorithmic": st["class_words"][c], "achieved": a,
-                         "unit": "Gop/s", "frac": a / alu, "roots": st["roots"][c]})
-    dom = max(kern, key=lambda k: k["ms"])
-    return {"workload": name, "n": n, "m": m, "alpha": len(depths) - 2, "omega": omega, "kmax": len(words) - 1,
-            "ms": ms, "edges_per_s": m / (ms / 1000.0), "counts": {"C1": words[1], "C2": words[2], "C3": words[3],
-                                                                  "C_max": str(max(words))},
-            "checks": {"C1_is_n": words[1] == n, "C2_is_m": words[2] == m, "C3_is_oracle_triangles": words[3] == T},
-            "sct": {"nodes": st["sct_nodes"], "leaves": st["sct_leaves"], "pivot_words": st["pivot_words"],
-                    "leaf_depth_mode": int(np.argmax(depths))},
-            "phases_ms": ph, "kernels": kern,
-            "roofline": {"bound": "alu", "kernel": dom["kernel"], "achieved": dom["achieved"], "peak": alu,
-                         "unit": "Gop/s", "frac": dom["frac"]},
-            "clocks": clocks,
-            "timing": "one orient + all-k count, CUDA events, classes serialised (policy.serial)"}
-
-
-def run_graph_replay(args, dev, reps=50):
-    """Global counts on a resident small graph (ER n=2000, avg degree 20,
-    one 30-clique), called repeatedly: the launch sequence issued directly
-    against the replay of its recorded CUDA graph (device time per call,
-    CUDA events around each call)."""
-    import torch
-    import paper_2001_06784_gb300 as pvt
-    from paper_2001_06784_gb300 import graphgen
-    name = "er2k_d20_clique30"
-    rp, col = graphgen.workload(name)
-    dag = pvt.orient(torch.from_numpy(rp).to(dev), torch.from_numpy(col.view(np.int32)).to(dev))
-    stream = torch.cuda.current_stream(dev)
-    out = torch.empty((dag.alpha + 2, dag.min_words), dtype=torch.int64, device=dev)
-    res = {"workload": name}
-    ref = None
-    for form in ("direct", "graph"):
-        dag.set_policy(graph=(form == "graph"))
-        ms = []
-        for i in range(reps + 3):
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            t0 = time.perf_counter()
-            e0.record(stream)
-            dag.count_global(out=out)
-            e1.record(stream)
-            torch.cuda.synchronize(dev)
-            if i >= 3:
-                ms.append((e0.elapsed_time(e1), (time.perf_counter() - t0) * 1000.0))
-        got = pvt.to_ints(out)
-        ref = got if ref is None else ref
-        assert got == ref, "graph replay differs from direct launches"
-        res[form] = {"device_ms": float(np.median([a for a, _ in ms])),
-                     "host_ms": float(np.median([b for _, b in ms])), "launches": dag.stats()["launches"]}
-    dag.free()
-    return res
-
-
-def run_serving(args, dev):
-    """The query server (continuous batching, large queries on the whole-GPU
-    direct path beside the batches) against one launch sequence per graph, on
-    the same query stream: closed-loop saturation throughput of each form
-    (every query submitted at once / one after another), then p50/p99
-    latency with Poisson arrivals at 0.8 x the plain form's saturation rate.
-    Every served result is checked word for word against the plain form's
-    (SHA-1 of the words), and the smallest queries against the oracle."""
-    import hashlib
-    import threading as th
-    import torch
-    import paper_2001_06784_gb300 as pvt
-    qs = serving_stream(args.serving_queries)
-    edges = sum(len(c) // 2 for _, c, _ in qs)
-
-    def digest(a):
-        return hashlib.sha1(np.ascontiguousarray(a).view(np.uint8)).hexdigest()
-
-    def plain_one(rp, col, kind):
-        rpd = torch.from_numpy(rp).to(dev, non_blocking=True)
-        cd = torch.from_numpy(col.view(np.int32)).to(dev, non_blocking=True)
-        dag = pvt.orient(rpd, cd)
-        out = dag.count_global() if kind == "global" else dag.count_local_edge()
-        host = out.cpu().numpy().view(np.uint64)
-        dag.free()
-        return host.reshape((1,) + host.shape) if kind == "global" else host
-
-    for rp, col, kind in qs[:3]:  # warm-up
-        plain_one(rp, col, kind)
-    torch.cuda.synchronize(dev)
-    # ---- closed loop, plain: one query after another
-    plain_hash = []
-    t0 = time.perf_counter()
-    for rp, col, kind in qs:
-        plain_hash.append(digest(plain_one(rp, col, kind)))
-    sat_plain_s = time.perf_counter() - t0
-    sat_qps = len(qs) / sat_plain_s
-    lam = 0.8 * sat_qps
-    arrivals = np.cumsum(np.random.default_rng(55).exponential(1.0 / lam, len(qs)))
-    small = sorted(range(len(qs)), key=lambda i: len(qs[i][1]))[:8]
-    kept = {}
-    cfg = dict(mem_budget=64 << 30, max_inflight=4096, max_batch=256, streams=4)
-    with pvt.Server(**cfg) as sv:
-        for rp, col, kind in qs[:3]:  # warm-up
-            t = sv.submit(rp, col, kind)
-            sv.wait(t)
-            sv.result(t)
-        # ---- closed loop, served: every query submitted at once
-        served_hash = [None] * len(qs)
-        t0 = time.perf_counter()
-        tickets = [sv.submit(rp, col, kind) for rp, col, kind in qs]
-        for i, t in enumerate(tickets):
-            sv.wait(t)
-            words, _ = sv.result(t)
-            served_hash[i] = digest(words)
-            if i in small:
-                kept[i] = words
-        sat_srv_s = time.perf_counter() - t0
-    mismatch = sum(a != b for a, b in zip(plain_hash, served_hash))
-    # oracle on the smallest queries
-    import oracle
-    oracle_ok = True
-    for i in small:
-        rp, col, kind = qs[i]
-        K = kept[i].shape[1] - 1
-        ref = oracle.count(rp, col, kmax=K, edge=kind == "edge")
-        want = ref["C"] if kind == "global" else oracle.to_int(ref["ce"])
-        got = pvt.to_ints(kept[i][0]) if kind == "global" else pvt.to_ints(kept[i])
-        oracle_ok = oracle_ok and got == want
-
-    # ---- open loop, plain: replayed in real time, one query at a time
-    lat_plain = []
-    t0 = time.perf_counter()
-    for (rp, col, kind), ta in zip(qs, arrivals):
-        now = time.perf_counter() - t0
-        if now < ta:
-            time.sleep(ta - now)
-        plain_one(rp, col, kind)
-        lat_plain.append(time.perf_counter() - t0 - ta)
-    plain_span = time.perf_counter() - t0
-
-    # ---- open loop, served: a submitter thread keeps the arrivals, latency
-    # measured inside the server (submit -> result ready)
-    lat_srv = [None] * len(qs)
-    with pvt.Server(**cfg) as sv:
-        for rp, col, kind in qs[:3]:  # warm-up
-            t = sv.submit(rp, col, kind)
-            sv.wait(t)
-            sv.result(t)
-        tickets = [None] * len(qs)
-        t0 = time.perf_counter()
-
-        def submitter():
-            for i, ((rp, col, kind), ta) in enumerate(zip(qs, arrivals)):
-                now = time.perf_counter() - t0
-                if now < ta:
-                    time.sleep(ta - now)
-                tickets[i] = sv.submit(rp, col, kind)
-
-        thr = th.Thread(target=submitter)
-        thr.start()
-        for i in range(len(qs)):
-            while tickets[i] is None:
-                time.sleep(0.0005)
-            sv.wait(tickets[i])
-            _, lat_srv[i] = sv.result(tickets[i])
-        thr.join()
-        srv_span = time.perf_counter() - t0
-
-    def summary(lat, span):
-        a = np.asarray(lat) * 1000.0
-        return {"p50_ms": float(np.percentile(a, 50)), "p99_ms": float(np.percentile(a, 99)),
-                "mean_ms": float(a.mean()), "throughput_qps": len(a) / span, "edges_per_s": edges / span}
-
-    return {"queries": len(qs), "stream": "ER or Chung-Lu, n log-uniform 100..50000, avg deg U[5,60], "
-                                          "global or per-edge (1/2 each), Poisson arrivals, seed 5",
-            "edges_total": edges,
-            "saturation": {"plain_qps": sat_qps, "served_qps": len(qs) / sat_srv_s,
-                           "plain_edges_per_s": edges / sat_plain_s, "served_edges_per_s": edges / sat_srv_s,
-                           "form": "closed loop: plain one query after another; served all submitted at once"},
-            "arrival_rate_qps": lam,
-            "plain": summary(lat_plain, plain_span), "batched": summary(lat_srv, srv_span),
-            "check": {"served_vs_plain_mismatches": int(mismatch), "oracle_sample": len(small),
                       "oracle_sample_ok": bool(oracle_ok)}}
 
 
@@ -1045,11 +828,14 @@ def main():
 
     def section(key, fn):
         """A secondary measurement; its failure is reported in its place
-        instead of losing the line."""
+        instead of losing the line.  Progress goes to stderr."""
+        t0 = time.perf_counter()
+        print(f"bench: {key} ...", file=sys.stderr, flush=True)
         try:
             out[key] = fn()
         except Exception as exc:  # noqa: BLE001 - reported in the JSON line
             out[key] = {"error": f"{type(exc).__name__}: {exc}"}
+        print(f"bench: {key} done in {time.perf_counter() - t0:.1f} s", file=sys.stderr, flush=True)
 
     # ---- launch cost: direct launches vs replay of the recorded CUDA graph
     if rank == 0:

@@ -599,8 +599,11 @@ __global__ void __launch_bounds__(TAIL_THREADS, 1) k_peel_tail(const int64_t *__
         }
         __syncthreads();
         if (threadIdx.x == 0) s_min[q] = NOT_REMOVED;  // read above by every thread
-        // ---- cascade (every warp)
-        {
+        // ---- cascade (every warp); none when the scan took every vertex
+        // left: decrements could then only reach removed vertices
+        if (*(volatile unsigned *)&s_tail == R) {
+            if (threadIdx.x == 0) s_done = R;
+        } else {
             unsigned claim = EMPTY;
             for (;;) {
                 int got = 0;  // 1: entry in i, 2: level done, 3: error
