@@ -35,12 +35,7 @@ SM_MAX_MHZ = 2070.0
 # kernel as it is now (summarised under profiles/, with the capture's date);
 # an entry is removed whenever its kernel changes, so that the bench line
 # reports null instead of a stale figure
-NCU_DRAM_BYTES = {
-    # k_lanes, the frame phase of the bench graph's all-k count (332,125,440
-    # read + 3,629,568 written), `ncu --set full` of `bench.py --profile lanes`
-    # (profiles/k_lanes_cl1m_m10m_b2.1_comm500.md)
-    "walk_frames": 335755008,
-}
+NCU_DRAM_BYTES = {}
 
 
 def parse():

@@ -31,7 +31,7 @@ namespace pvt {
 
 constexpr int LANE_WPB = 8;     // warps per block
 constexpr int LSTK = 32;        // per-lane stack slots (a label of s <= 32 keeps at most 31 pending)
-constexpr unsigned LANE_DONATE_EVERY = 32;  // node steps between looks at the ring queue
+constexpr unsigned LANE_DONATE_EVERY = 16;  // node steps between looks at the ring queue
 constexpr unsigned LANE_DONATE_MAX = 4;     // entries one look may donate
 
 struct LaneWork {
