@@ -102,6 +102,9 @@ constexpr unsigned BULK_MIN = 4096, BULK_LANE_MAX = 64;
 // Rows are read PEEL_UNROLL entries per lane at a time: every load, then
 // every degree decrement, is in flight before the first result is used.
 constexpr int PEEL_UNROLL = 4;
+// A warp adds its processed entries to done at least every DONE_REPORT
+// entries (and before every claim).
+constexpr unsigned DONE_REPORT = 64;
 
 // One removal found by a decrement (bulk phase: single pushes, no warp
 // aggregation).
@@ -432,7 +435,14 @@ __global__ void __launch_bounds__(1024, 1) k_peel(int64_t n, const int64_t *__re
                         pos += __popc(bp[t]);
                     }
                 }
-                if (lane == 0) ++ndone;
+                if (lane == 0 && ++ndone >= DONE_REPORT) {
+                    // a long chain of kept vertices (a path graph's level is
+                    // one chain) reports its progress as it goes: waiting
+                    // warps give up after CASCADE_LIMIT_NS without any
+                    __threadfence();  // their pushes are counted before they are done
+                    atomicAdd(&st->done, ndone);
+                    ndone = 0;
+                }
             }
         }
         mnext = __reduce_min_sync(FULL, mnext);
